@@ -1,0 +1,35 @@
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: CPU test that takes more than ~20 s")
+
+
+@pytest.fixture(scope="session")
+def torch_philox(tmp_path_factory):
+    """Callable (seed, subsequence, offset) triples -> words, backed by PyTorch's
+    header-only ``at::philox_engine`` compiled for the host."""
+    import numpy as np
+    import torch
+
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    exe = str(tmp_path_factory.mktemp("tpd") / "torch_philox_dump")
+    src = os.path.join(ROOT, "tests", "helpers", "torch_philox_dump.cpp")
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", inc, src, "-o", exe], check=True)
+
+    def run(triples):
+        text = "\n".join(f"{int(s)} {int(q)} {int(o)}" for s, q, o in triples) + "\n"
+        out = subprocess.run([exe], input=text, capture_output=True, text=True, check=True)
+        return np.array([[int(v) for v in line.split()] for line in out.stdout.splitlines()],
+                        dtype=np.uint32).reshape(-1, 4)
+
+    return run
