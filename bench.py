@@ -1,0 +1,422 @@
+"""Benchmark: integrand samples/s of batched multi-function direct Monte Carlo.
+
+Default workload (N=1): the paper's GPU test (Eq. 1, Fig. 1) at its stated
+size, 100 four-dimensional harmonics x 10^6 samples, with the paper's 10
+independent evaluations (Philox keys 0..9) in one table: 10^9 samples per step.
+One step = one pass of the whole path over that table: reset the work counter,
+the persistent FP32 sampling launch over all (integrand, chunk) items, the FP64
+merge.  Inputs (the precomputed descriptor table) are resident on the device
+when the timed region starts.
+
+Also reported on the same line: the plain form (one FP64 launch per integrand)
+on the same table, the 10^4-integrand mixed table (batched and plain), the end-
+to-end rate through zmc_integrate with host buffers, a short serving run
+(p50/p99 job latency), the roofline of the dominant kernel and the FP64 oracle
+on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2104_10073_gb300 import workloads as W  # noqa: E402
+
+METRIC = "integrand samples/s (G/s) batched vs plain on 1 GB300; p50/p99 job latency"
+UNIT = "Gsamples/s"
+WORKLOAD = "fig1-harmonics-100x1e6-x10-repeats"
+
+# Algorithmic 32-bit operations per sample of a d-dimensional harmonic (the
+# dominant kernel of the default workload), counted from the method's minimal
+# steps: Philox4x32-10 = 10 rounds x (2 widening multiplies + 2 three-way XORs)
+# per 4 words -> 10 d; per coordinate: 23-bit mask + 64-bit fixed-point
+# multiply-add (2) -> 3 d; phase fraction, quadrant and remainder -> 6;
+# sin and cos polynomials -> 10; quadrant rotation and a cos + b sin -> 8;
+# shifted sums -> 3.
+def harmonic_ops_per_sample(d: int) -> int:
+    return 10 * d + 3 * d + 6 + 10 + 8 + 3
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_rate(rows, threads=0):
+    """FP64 oracle samples/s over ``rows`` on the host cores."""
+    import oracle
+
+    t0 = time.perf_counter()
+    _, used = oracle.integrate(rows, threads=threads)
+    dt = time.perf_counter() - t0
+    return W.total_samples(rows) / dt, used, dt
+
+
+def fig1_table(rank: int):
+    # weak scaling: rank r evaluates its own 10 repeats (keys 10r .. 10r+9)
+    return W.harmonic_fig1(10**6, seeds=range(10 * rank, 10 * rank + 10))
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle on the host cores, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    sample = W.harmonic_fig1(10**5, seeds=[0])  # 100 integrands x 10^5 samples per step
+    for _ in range(args.warmup):
+        oracle_rate(sample)
+    times = []
+    used = 0
+    for _ in range(args.steps):
+        _, used, dt = oracle_rate(sample)
+        times.append(dt)
+    n = W.total_samples(sample)
+    value = n * len(times) / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "100 integrands x 1e5 samples per step",
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": "Fig. 1 harmonics, key 0, 100 x 1e5 samples per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_plan(zmc, torch, ctx, plan, steps, flush):
+    """Device time per step and of the sampling stage, CUDA events on ctx.stream."""
+    s = ctx.stream
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(s):
+            flush.zero_()  # write > L2 between steps
+        ev[k][0].record(s)
+        zmc.zmc_plan_run(plan, zmc.ZMC_STAGE_SAMPLE)
+        ev[k][1].record(s)
+        zmc.zmc_plan_run(plan, zmc.ZMC_STAGE_MERGE)
+        ev[k][2].record(s)
+    s.synchronize()
+    step = [ev[k][0].elapsed_time(ev[k][2]) for k in range(steps)]
+    kern = [ev[k][0].elapsed_time(ev[k][1]) for k in range(steps)]
+    return step, kern
+
+
+def run_native(args, world, rank, local):
+    import torch
+
+    from paper_2104_10073_gb300 import build
+    from paper_2104_10073_gb300 import zmc
+
+    build.build()
+    torch.cuda.set_device(local)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+
+    # CPU baseline first (host threads only; no process is forked after CUDA init)
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        sample = W.harmonic_fig1(10**6, seeds=[0])
+        rate, used, dt = oracle_rate(sample)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"Fig. 1 harmonics, key 0, 100 x 1e6 samples ({dt:.1f} s)"}
+
+    ctx = zmc.Context(arena_bytes=2 << 30, device=local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    tab = fig1_table(rank)
+    n_samples = W.total_samples(tab)
+    plan = zmc.zmc_plan_create(ctx.handle, tab)
+    info = zmc.zmc_plan_info_get(plan)
+    for _ in range(max(args.warmup, 3)):
+        zmc.zmc_plan_run(plan)
+    ctx.stream.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    step_ms, kern_ms = time_plan(zmc, torch, ctx, plan, args.steps, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = max_over_ranks(world, sum(step_ms) / len(step_ms))
+    kms = sum(kern_ms) / len(kern_ms)
+    total = sum_over_ranks(world, float(n_samples))
+    value = total / (ms / 1e3) / 1e9
+    res = zmc.zmc_plan_results(plan, len(tab))
+    assert np.all(res["status"] == 0)
+
+    # plain FP64 form, same table, one launch per integrand
+    plain_steps = max(1, min(args.steps, 3))
+    zmc.zmc_plan_run_plain(plan)
+    ctx.stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(plain_steps):
+        zmc.zmc_plan_run_plain(plan)
+    e1.record(ctx.stream)
+    ctx.stream.synchronize()
+    plain_ms = e0.elapsed_time(e1) / plain_steps
+    zmc.zmc_plan_destroy(plan)
+
+    # end to end through the public blocking call: host table in, host results out
+    e2e_t = []
+    for k in range(args.steps + 1):
+        t0 = time.perf_counter()
+        out = zmc.zmc_integrate(ctx.handle, tab)
+        if k > 0:
+            e2e_t.append(time.perf_counter() - t0)
+    assert np.all(out["status"] == 0)
+    e2e_s = max_over_ranks(world, sum(e2e_t) / len(e2e_t))
+
+    # the 10^4-integrand mix (batched and plain), rank 0 only
+    mixed = None
+    if rank == 0 and not args.skip_mixed:
+        mt = W.mixed(10**4)
+        mp = zmc.zmc_plan_create(ctx.handle, mt)
+        zmc.zmc_plan_run(mp)
+        ctx.stream.synchronize()
+        st, _ = time_plan(zmc, torch, ctx, mp, 3, flush)
+        zmc.zmc_plan_run_plain(mp)
+        ctx.stream.synchronize()
+        e0.record(ctx.stream)
+        zmc.zmc_plan_run_plain(mp)
+        e1.record(ctx.stream)
+        ctx.stream.synchronize()
+        pms = e0.elapsed_time(e1)
+        ns = W.total_samples(mt)
+        mixed = {"workload": "mixed-1e4-integrands-d1..7-logN4..7", "samples": ns,
+                 "batched_gsps": ns / (statistics.median(st) / 1e3) / 1e9,
+                 "plain_gsps": ns / (pms / 1e3) / 1e9,
+                 "batched_ms": statistics.median(st), "plain_ms": pms}
+        mixed["batched_over_plain"] = mixed["batched_gsps"] / mixed["plain_gsps"]
+        zmc.zmc_plan_destroy(mp)
+
+    serving = None
+    if rank == 0 and not args.skip_serving:
+        serving = run_serving(zmc, local, args.serving_rate, args.serving_seconds)
+    ctx.close()
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (the harmonic family's persistent launch)
+    sm_clock = peaks.get("sm_max_mhz", 2070.0)
+    sms = info["sms"]
+    peak_gops = sms * 128 * sm_clock * 1e6 / 1e9
+    ops = harmonic_ops_per_sample(4) * n_samples
+    achieved = ops / (kms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "integrands": len(tab), "samples_per_step": n_samples,
+                   "quads_per_lane": info["quads_per_lane"], "chunks": info["n_chunks"],
+                   "grid": info["grid"], "block": info["block"],
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)"},
+        "plain": {"value": n_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT,
+                  "ms_per_step": plain_ms, "dtype": "f64",
+                  "form": "one FP64 kernel launch per integrand + merge"},
+        "batched_over_plain": plain_ms / (sum(step_ms) / len(step_ms)),
+        "mixed": mixed,
+        "serving": serving,
+        "e2e": {"value": total / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": len(tab) * W.DESC_DTYPE.itemsize,
+                "d2h_bytes_per_step": len(tab) * 32,
+                "path": "zmc_integrate (host table in, host results out)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved / peak_gops, "traffic": None,
+                     "kernel": "zmc_batched_kernel<HARMONIC>",
+                     "kernel_ms": kms,
+                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz issue",
+                     "ops_per_sample": harmonic_ops_per_sample(4)},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(zmc, device, rate_hz, seconds):
+    """Poisson job stream through zmc_submit/zmc_poll; per-job latency submit->result."""
+    jobs = W.serving_stream(rate_hz, seconds, max_fns=1000)
+    ctx = zmc.Context(arena_bytes=8 << 30, device=device, serving=True)
+    done = {}
+    lock = threading.Lock()
+    pending = []
+
+    def poller():
+        while True:
+            with lock:
+                if not pending and stop[0]:
+                    return
+                items = list(pending)
+            for jid, n, ts in items:
+                st, _ = zmc.zmc_poll(ctx.handle, jid, n, wait_ms=0)
+                if st == zmc.ZMC_OK:
+                    done[jid] = time.perf_counter() - ts
+                    with lock:
+                        pending.remove((jid, n, ts))
+            time.sleep(0.0005)
+
+    stop = [False]
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    samples = 0
+    for at, tab in jobs:
+        while time.perf_counter() - t0 < at:
+            time.sleep(0.0002)
+        jid = zmc.zmc_submit(ctx.handle, tab)
+        samples += W.total_samples(tab)
+        with lock:
+            pending.append((jid, len(tab), time.perf_counter()))
+    stop[0] = True
+    th.join()
+    wall = time.perf_counter() - t0
+    ctx.close()
+    lat = sorted(done.values())
+    if not lat:
+        return None
+    return {"rate_jobs_per_s": rate_hz, "jobs": len(lat), "seconds": wall,
+            "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "samples_per_s": samples / wall / 1e9, "unit": "Gsamples/s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-mixed", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serving-rate", type=float, default=100.0)
+    ap.add_argument("--serving-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    world, rank, local = (int(os.environ.get("WORLD_SIZE", "1")),
+                          int(os.environ.get("RANK", "0")),
+                          int(os.environ.get("LOCAL_RANK", "0")))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_setup()
+    run_native(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

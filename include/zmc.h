@@ -1,0 +1,223 @@
+/*
+ * zmc.h -- C ABI of the GB300 multi-function direct Monte Carlo integrator.
+ *
+ * The method is the multi-function mode of ZMCintegral-v5.1 (arXiv
+ * 2104.10073): many integrands, each with its own form, dimension and box
+ * domain (Sec. "Summary of revisions": Eq. 1, Eq. 2 and the text after it),
+ * integrated together by direct Monte Carlo, one estimate per integrand
+ * (Sec. "Solution method"), with the estimate's spread reported beside it
+ * (Fig. 1 caption).
+ *
+ * For integrand f on the box B = prod_i [lo_i, hi_i] with N samples:
+ *     estimate = V * mean,   V = prod_i (hi_i - lo_i),  mean = (1/N) sum_s f(x_s)
+ *     stderr   = V * sqrt(M2 / (N (N - 1))),            M2 = sum_s (f(x_s) - mean)^2
+ * Sample s of an integrand with dimension d, key `seed` and stream `stream_id`
+ * uses words w = s*d + i (i < d) of a Philox4x32-10 stream: word w is lane
+ * (w mod 4) of Philox4x32-10(counter = (b mod 2^32, b div 2^32, stream_id, 0),
+ * key = (seed mod 2^32, seed div 2^32)), b = w div 4, and coordinate i is
+ * x_i = lo_i + (hi_i - lo_i) * (word & 0x7FFFFF) * 2^-23.  The results are
+ * therefore a pure function of the descriptor table: they do not depend on
+ * launch configuration, on which other integrands share a launch, or on how
+ * work is split between launches.
+ *
+ * Conventions for every entry point:
+ *   - Pointers are plain host pointers unless the argument says "device".
+ *     The caller owns every array it passes; the library copies what it keeps.
+ *   - Every call returns a zmc_status.  On failure zmc_last_error() gives a
+ *     one-line reason.  A CUDA error returns ZMC_ECUDA and leaves the context
+ *     unusable (every later call on it returns ZMC_ECUDA); destroy it.
+ *   - A context serialises its calls internally; different contexts are
+ *     independent.
+ */
+#ifndef ZMC_H
+#define ZMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZMC_MAX_DIM 7
+#define ZMC_NPARAM 40
+
+/* Integrand families.  x is the point, d the dimension; parameter layout in
+ * zmc_desc.p:
+ *   ZMC_HARMONIC  a cos(k.x) + b sin(k.x)        (Eq. 1)   p[0]=a p[1]=b p[2+i]=k_i
+ *   ZMC_ABSLIN    a |c.x|                        (Eq. 2)   p[0]=a p[1+i]=c_i
+ *   ZMC_GAUSS     A exp(-|x-mu|^2 / (2 sigma^2))           p[0]=A p[1]=sigma p[2+i]=mu_i
+ *   ZMC_POLY      prod_i sum_{j<=deg} c_ij x_i^j          p[5i+j]=c_ij              */
+enum zmc_family { ZMC_HARMONIC = 0, ZMC_ABSLIN = 1, ZMC_GAUSS = 2, ZMC_POLY = 3 };
+
+typedef enum zmc_status {
+    ZMC_OK = 0,
+    ZMC_EINVAL = 1,    /* bad argument or descriptor                               */
+    ZMC_ENOMEM = 2,    /* the request can never fit the device memory budget       */
+    ZMC_EAGAIN = 3,    /* zmc_poll: the job is not finished yet                    */
+    ZMC_ETIMEOUT = 4,  /* zmc_poll: waited wait_ms and the job is still running    */
+    ZMC_ECUDA = 5,     /* a CUDA call failed; the context is poisoned              */
+    ZMC_ENOTFOUND = 6, /* unknown or already collected job id                      */
+    ZMC_ECLOSED = 7,   /* the context is shutting down / job was cancelled         */
+    ZMC_ENOSYS = 8     /* feature not available in this build                      */
+} zmc_status;
+
+/* One integrand (464 bytes, naturally aligned, no padding beyond `deg`).
+ * Valid: family in 0..3, 1 <= dim <= 7, n_samples >= 1, lo_i < hi_i finite,
+ * deg <= 4 (ZMC_POLY; 0 otherwise), sigma > 0 (ZMC_GAUSS), finite parameters.
+ * Entries of lo/hi/p beyond the family's use are ignored.                      */
+typedef struct zmc_desc {
+    uint32_t family;
+    uint32_t dim;
+    uint32_t stream_id; /* Philox counter word 2: selects the integrand's stream */
+    uint32_t deg;
+    uint64_t n_samples;
+    uint64_t seed;      /* Philox key                                             */
+    double lo[ZMC_MAX_DIM];
+    double hi[ZMC_MAX_DIM];
+    double p[ZMC_NPARAM];
+} zmc_desc;
+
+/* One result.  status is ZMC_OK, or ZMC_ECLOSED for a cancelled job's rows.
+ * stderr_ is NaN when n == 1 (the spread of one sample is undefined).        */
+typedef struct zmc_result {
+    double estimate;
+    double stderr_;
+    uint64_t n;
+    int32_t status;
+    int32_t reserved;
+} zmc_result;
+
+typedef struct zmc_options {
+    uint64_t mem_budget_bytes;   /* device arena; 0 -> 1 GiB                          */
+    void *arena;                 /* optional caller-owned DEVICE buffer of
+                                    mem_budget_bytes bytes (e.g. a framework tensor),
+                                    256-byte aligned; NULL -> the library allocates */
+    void *stream;                /* cudaStream_t for all work; NULL -> the library
+                                    creates a non-blocking stream                   */
+    uint32_t max_chunks_per_iter;/* serving: chunks per persistent launch; 0 -> auto */
+    uint32_t autotune;           /* 1: time launch shapes on first use and cache     */
+    int32_t device;              /* CUDA device ordinal                              */
+    uint32_t quads_per_lane;     /* chunk = 128 * quads_per_lane samples; 0 -> 16.
+                                    Results are bit-identical for a fixed value and
+                                    agree within rounding across values.            */
+    const char *tune_cache_path; /* autotune JSON cache; NULL -> no file             */
+    uint32_t serving;            /* 1: start the serving thread (zmc_submit/poll)    */
+    uint32_t reserved;
+} zmc_options;
+
+typedef struct zmc_ctx zmc_ctx;
+typedef struct zmc_plan zmc_plan;
+
+typedef struct zmc_plan_info {
+    uint64_t n_fn;
+    uint64_t n_chunks;     /* work items of the persistent launch                  */
+    uint64_t n_samples;    /* total samples over all integrands                    */
+    uint32_t grid;         /* persistent launch shape                              */
+    uint32_t block;
+    uint32_t quads_per_lane;
+    uint32_t sms;
+} zmc_plan_info;
+
+typedef struct zmc_serving_stats {
+    uint64_t submitted, completed, cancelled, queued, running;
+    uint64_t iterations;         /* persistent launches so far                     */
+    uint64_t samples_done;
+    uint64_t arena_used_bytes, arena_bytes;
+} zmc_serving_stats;
+
+/* Fill *opt with defaults (1 GiB arena, own stream, device 0, no autotune). */
+zmc_status zmc_default_options(zmc_options *opt);
+
+/* Create a context on opt->device.  Allocates the arena (unless given), a
+ * pinned host staging buffer and, if opt->serving, starts the scheduler thread.
+ * *out is set on success and must be released with zmc_destroy. */
+zmc_status zmc_create(const zmc_options *opt, zmc_ctx **out);
+
+/* Stop the serving thread (pending jobs are cancelled), wait for the stream,
+ * free everything the context owns.  NULL is accepted. */
+zmc_status zmc_destroy(zmc_ctx *ctx);
+
+/* Reason for the last failure on this thread (ctx may be NULL).  Valid until
+ * the next call on this thread. */
+const char *zmc_last_error(zmc_ctx *ctx);
+
+/* Blocking batched integration of n descriptors (host arrays in and out):
+ * validate and precompute on the host, copy the table to the device, run the
+ * persistent FP32 sampling launch over all (integrand, chunk) work items and
+ * the FP64 merge, copy the n results back. */
+zmc_status zmc_integrate(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_result *out);
+
+/* Same results contract computed the plain way: one FP64 direct-MC kernel
+ * launch per integrand (FP64 map and evaluation, FP64 reductions), then one
+ * merge launch.  The baseline the batched form is measured against. */
+zmc_status zmc_integrate_plain(zmc_ctx *ctx, const zmc_desc *desc, size_t n,
+                               zmc_result *out);
+
+/* Serving (continuous batching).  zmc_submit copies the n descriptors into a
+ * job and returns its id at once; the scheduler admits queued jobs as device
+ * memory frees up, keeps their partial sums on the device, and gives every
+ * persistent launch a share of the chunks of every admitted job.  A job that
+ * alone exceeds the memory budget is refused with ZMC_ENOMEM.
+ * Requires opt->serving = 1. */
+zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *job_id);
+
+/* Collect a job.  wait_ms = 0: return ZMC_EAGAIN if it is not finished;
+ * wait_ms > 0: wait up to that long, then ZMC_ETIMEOUT; wait_ms < 0: wait until
+ * done.  On ZMC_OK the job's n results are written to out (n entries, in
+ * submission order) and the id is released (a second poll gives ZMC_ENOTFOUND). */
+zmc_status zmc_poll(zmc_ctx *ctx, uint64_t job_id, zmc_result *out, int32_t wait_ms);
+
+/* Cancel a queued or running job; a later poll returns ZMC_ECLOSED. */
+zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id);
+
+zmc_status zmc_serving_stats_get(zmc_ctx *ctx, zmc_serving_stats *out);
+
+/* Device-resident plan: the descriptor table precomputed and uploaded once,
+ * its partial-sum records and results kept in the arena, so the sampling and
+ * merge launches can be replayed (as a CUDA graph) without host traffic. */
+zmc_status zmc_plan_create(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out);
+
+#define ZMC_STAGE_SAMPLE 1u /* reset the work counter + persistent sampling launch */
+#define ZMC_STAGE_MERGE 2u  /* FP64 merge of every integrand's chunk records       */
+#define ZMC_STAGE_ALL 3u    /* both, replayed as one captured CUDA graph           */
+
+/* Enqueue the chosen stages on the context stream; returns without waiting. */
+zmc_status zmc_plan_run(zmc_plan *plan, uint32_t stages);
+
+/* Enqueue the plain FP64 form (one launch per integrand + merge). */
+zmc_status zmc_plan_run_plain(zmc_plan *plan);
+
+/* Wait for the stream and copy the plan's n results to the host. */
+zmc_status zmc_plan_results(zmc_plan *plan, zmc_result *out);
+
+/* Device pointer to the plan's results (n zmc_result rows). */
+zmc_status zmc_plan_device_results(zmc_plan *plan, void **device_ptr);
+
+zmc_status zmc_plan_info_get(const zmc_plan *plan, zmc_plan_info *out);
+zmc_status zmc_plan_destroy(zmc_plan *plan);
+
+/* Philox4x32-10 of n counters (host array, n x 4 words) under n keys (n x 2),
+ * computed by the same device routine the sampling kernel uses; out is n x 4. */
+zmc_status zmc_philox4x32_10(zmc_ctx *ctx, const uint32_t *ctr, const uint32_t *key,
+                             uint32_t *out, size_t n);
+
+/* FP32 values f(x_s) of samples s in [s_begin, s_begin + count) of one
+ * integrand, computed by the sampling kernel's own generation, map and
+ * evaluation code; out has count floats (host). */
+zmc_status zmc_eval_samples(zmc_ctx *ctx, const zmc_desc *desc, uint64_t s_begin,
+                            uint32_t count, float *out);
+
+/* Host-only check of n descriptors with the rules listed at zmc_desc (no GPU
+ * needed).  Returns ZMC_OK, or ZMC_EINVAL with *bad_index (if non-NULL) set to
+ * the first rejected row. */
+zmc_status zmc_validate(const zmc_desc *desc, size_t n, size_t *bad_index);
+
+/* sizeof checks for foreign-language bindings. */
+size_t zmc_desc_size(void);
+size_t zmc_result_size(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZMC_H */

@@ -1,0 +1,104 @@
+"""Fit the FP32 polynomials for sin(2 pi t) and cos(2 pi t) on |t| <= 1/8 turn.
+
+The kernels reduce every phase to a quarter-turn index q and a remainder t in
+[-1/8, 1/8] turns (exactly, in fixed point), then evaluate
+
+    sin(2 pi t) ~= t * (S0 + S1 t^2 + S2 t^4 + S3 t^6)
+    cos(2 pi t) ~= C0 + C1 t^2 + C2 t^4 + C3 t^6 + C4 t^8
+
+The coefficients are found here by a Remez exchange on the weighted error in
+the variable z = t^2 (absolute error for cos; error of sin(2 pi t)/t weighted by
+|t| for sin), carried out in 50-digit arithmetic, then rounded to binary32.
+The script prints the maximum error of the rounded polynomials evaluated in
+FP64 on a dense grid and writes ``zmc_sincos_coeffs.h``.
+
+Run from the repository root:  python paper_2104_10073_gb300/csrc/gen_sincos.py
+"""
+import os
+
+import mpmath
+import numpy as np
+
+mpmath.mp.dps = 50
+T_MAX = mpmath.mpf(1) / 8
+Z_MAX = T_MAX**2
+
+
+def remez(target, weight, n_coef, iters=30):
+    """Minimax polynomial p(z) = sum c_j z^j of weight(z) * (target(z) - p(z)) on [0, Z_MAX]."""
+    m = n_coef + 1
+    # Chebyshev extrema as the first reference
+    ref = [Z_MAX * (1 - mpmath.cos(mpmath.pi * i / (m - 1))) / 2 for i in range(m)]
+    coef = None
+    for _ in range(iters):
+        A = mpmath.matrix(m, m)
+        rhs = mpmath.matrix(m, 1)
+        for i, z in enumerate(ref):
+            for j in range(n_coef):
+                A[i, j] = z**j
+            A[i, n_coef] = (-1) ** i / weight(z)
+            rhs[i] = target(z)
+        sol = mpmath.lu_solve(A, rhs)
+        coef = [sol[j] for j in range(n_coef)]
+
+        def err(z):
+            return weight(z) * (target(z) - sum(c * z**j for j, c in enumerate(coef)))
+
+        # new reference: extrema of the error on a fine grid, one per sign run
+        grid = [Z_MAX * (1 - mpmath.cos(mpmath.pi * i / 4000)) / 2 for i in range(4001)]
+        vals = [err(z) for z in grid]
+        runs = []
+        start = 0
+        for i in range(1, len(grid) + 1):
+            if i == len(grid) or mpmath.sign(vals[i]) != mpmath.sign(vals[start]):
+                best = max(range(start, i), key=lambda k: abs(vals[k]))
+                runs.append(best)
+                start = i
+        if len(runs) < m:
+            break
+        # keep m alternating extrema with the largest magnitudes
+        while len(runs) > m:
+            if abs(vals[runs[0]]) < abs(vals[runs[-1]]):
+                runs.pop(0)
+            else:
+                runs.pop()
+        ref = [grid[k] for k in runs]
+    return coef
+
+
+def sin_target(z):
+    t = mpmath.sqrt(z)
+    if t == 0:
+        return 2 * mpmath.pi
+    return mpmath.sin(2 * mpmath.pi * t) / t
+
+
+def main():
+    s = remez(sin_target, lambda z: mpmath.sqrt(z) if z > 0 else mpmath.mpf("1e-30"), 4)
+    c = remez(lambda z: mpmath.cos(2 * mpmath.pi * mpmath.sqrt(z)), lambda z: 1, 5)
+    s32 = [np.float32(float(v)) for v in s]
+    c32 = [np.float32(float(v)) for v in c]
+    t = np.linspace(-1 / 8, 1 / 8, 200001)
+    z = t * t
+    ps = t * sum(float(v) * z**j for j, v in enumerate(s32))
+    pc = sum(float(v) * z**j for j, v in enumerate(c32))
+    es = np.max(np.abs(ps - np.sin(2 * np.pi * t)))
+    ec = np.max(np.abs(pc - np.cos(2 * np.pi * t)))
+    print(f"max |sin err| {es:.3e}  max |cos err| {ec:.3e}")
+    here = os.path.dirname(os.path.abspath(__file__))
+    lines = [
+        "// Generated by gen_sincos.py: Remez fits of sin(2 pi t)/t and cos(2 pi t) in",
+        "// z = t^2 on |t| <= 1/8 turn, rounded to binary32.  Max error of the rounded",
+        f"// polynomials in exact arithmetic: sin {es:.2e}, cos {ec:.2e}.",
+        "#pragma once",
+    ]
+    for j, v in enumerate(s32):
+        lines.append(f"#define ZMC_SIN_C{j} {float(v).hex()}f  // {float(v):.9e}")
+    for j, v in enumerate(c32):
+        lines.append(f"#define ZMC_COS_C{j} {float(v).hex()}f  // {float(v):.9e}")
+    with open(os.path.join(here, "zmc_sincos_coeffs.h"), "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+if __name__ == "__main__":
+    main()

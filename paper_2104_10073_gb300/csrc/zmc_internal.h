@@ -1,0 +1,114 @@
+// Internal device-side layouts of the GB300 multi-function Monte Carlo path.
+//
+// The host runtime (zmc_runtime.cpp) turns each public zmc_desc into one FnDev
+// (FP32 evaluation constants derived in FP64) and the kernels (zmc_kernels.cu)
+// read only FnDev, Entry and LaunchHdr.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "zmc.h"
+
+namespace zmc {
+
+constexpr int kMaxDim = 7;
+constexpr int kWarp = 32;
+
+// Variant code: family in bits 4..5, dimension in bits 0..2, polynomial degree in
+// bits 6..8.  The sampling kernel dispatches one specialised body per variant.
+__host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t dim,
+                                                    uint32_t deg) {
+  return (family << 4) | dim | (deg << 6);
+}
+
+// One integrand as the sampling kernel sees it (384 bytes, 16-byte aligned).
+//
+// Payload words w[] by family (FP32 unless noted; "hi/lo" pairs are an FP64
+// constant split as hi = fl32(c), lo = fl32(c - hi), so that an FMA chain over
+// both halves carries the constant to ~2^-48 relative):
+//   HARMONIC  T_i (u64 two's complement) at w[2i], i < 7: k_i (hi_i-lo_i)/(2 pi) * 2^41,
+//             i.e. turns per unit of the 23-bit sample integer m_i, in units of
+//             2^-64 turn;  P0 (u64) at w[14]: frac(k.lo/(2 pi)) * 2^64;
+//             a w[16], b w[17], -a w[18].
+//   ABSLIN    s = C + sum_i g_i v_i, v_i = 1 + m_i 2^-23 in [1, 2):
+//             g_i = c_i (hi_i - lo_i):  hi w[i], lo w[7+i];
+//             C = sum_i c_i (lo_i - (hi_i - lo_i)):  hi w[14], lo w[15];  a w[16].
+//   GAUSS     t_i = e_i + h_i v_i = (x_i - mu_i) beta, beta^2 = log2(e) / (2 sigma^2):
+//             h_i = (hi_i - lo_i) beta: hi w[i], lo w[7+i];
+//             e_i = (lo_i - (hi_i - lo_i) - mu_i) beta: hi w[14+i], lo w[21+i];
+//             A w[28];  f = A 2^(-sum t_i^2).
+//   POLY      factor i re-expanded in u_i = m_i 2^-23 in [0, 1):
+//             q_i(u) = sum_j e_ij u^j; e_ij hi at w[5i+j], lo at w[35+5i+j].
+struct alignas(16) FnDev {
+  uint32_t variant;
+  uint32_t stream_id;
+  uint32_t key0, key1;
+  uint64_t n_samples;
+  float2 *rec;        // chunk records (mean, M2) of this integrand, one per chunk
+  zmc_result *out;    // result row written by the merge kernel
+  double volume;      // prod (hi_i - lo_i), FP64
+  uint32_t pad[4];
+  uint32_t w[80];
+};
+static_assert(sizeof(FnDev) == 384, "FnDev layout");
+
+// A contiguous run of chunks of one integrand inside one persistent launch.
+struct Entry {
+  uint64_t item_begin;   // first work-item index of this run in the launch
+  const FnDev *fn;
+  uint64_t chunk_begin;  // first chunk of the integrand covered by this run
+};
+static_assert(sizeof(Entry) == 24, "Entry layout");
+
+// Per-launch header, device resident so that a captured graph can be replayed
+// with new contents.  The work items of a launch are ordered by family; family f
+// owns items [item_begin[f], item_end[f]) and is drained by its own persistent
+// kernel through counter[f].
+struct LaunchHdr {
+  unsigned long long counter[4];     // per-family item dispensers (zeroed before a launch)
+  unsigned long long item_begin[4];
+  unsigned long long item_end[4];
+  uint32_t n_entries;
+  uint32_t n_merge;                  // integrands to merge after this launch
+  uint32_t quads_per_lane;           // chunk = 128 * quads_per_lane samples
+  uint32_t pad;
+};
+
+// FP64 descriptor of the plain per-integrand kernel (passed by value).
+struct PlainFn {
+  uint32_t family, dim, stream_id, deg;
+  uint32_t key0, key1;
+  uint64_t n_samples;
+  double lo[kMaxDim];
+  double w[kMaxDim];
+  double p[ZMC_NPARAM];
+};
+
+// Plain-form merge job (one per integrand): its per-block (n, mean, M2) records.
+struct PlainJob {
+  const double *rec;
+  uint32_t nblk;
+  uint32_t pad;
+  double volume;
+  zmc_result *out;
+};
+
+// Launch wrappers (zmc_kernels.cu).  All return the launch's cudaError_t.
+cudaError_t launch_batched(int family, const Entry *entries, LaunchHdr *hdr, unsigned grid,
+                           unsigned block, cudaStream_t stream);
+cudaError_t launch_merge(const FnDev *const *fns, const LaunchHdr *hdr, unsigned grid,
+                         cudaStream_t stream);
+cudaError_t launch_plain(const PlainFn &fn, double *block_rec, unsigned grid,
+                         cudaStream_t stream);
+cudaError_t launch_plain_merge(const PlainJob *jobs, uint32_t n, cudaStream_t stream);
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, size_t n,
+                          cudaStream_t stream);
+cudaError_t launch_eval(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out,
+                        cudaStream_t stream);
+int batched_max_blocks_per_sm(int family, int block);
+unsigned plain_grid(const PlainFn &fn, int sms);
+
+}  // namespace zmc

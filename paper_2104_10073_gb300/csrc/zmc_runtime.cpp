@@ -1,0 +1,795 @@
+// zmc_runtime.cpp -- host runtime of the GB300 multi-function Monte Carlo
+// library: descriptor validation and FP64 precompute, the device arena, plans
+// (device-resident tables replayed as CUDA graphs), and the C ABI entry points
+// other than serving (zmc_serving.cpp).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <numeric>
+
+#include "zmc_runtime.h"
+
+namespace zmc {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+zmc_status set_error(zmc_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+zmc_status ctx_cuda_fail(zmc_ctx *ctx, cudaError_t err, const char *what) {
+  if (ctx) ctx->poisoned = true;
+  return set_error(ZMC_ECUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+#define ZMC_CUDA(ctx, call)                                              \
+  do {                                                                   \
+    cudaError_t zmc_err_ = (call);                                       \
+    if (zmc_err_ != cudaSuccess) return ctx_cuda_fail(ctx, zmc_err_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- arena
+void Arena::init(char *base, size_t bytes) {
+  std::lock_guard<std::mutex> g(mu_);
+  base_ = base;
+  size_ = bytes & ~static_cast<size_t>(255);
+  used_ = 0;
+  free_.clear();
+  allocated_.clear();
+  if (size_) free_[0] = size_;
+}
+
+void *Arena::alloc(size_t bytes) {
+  std::lock_guard<std::mutex> g(mu_);
+  bytes = (std::max<size_t>(bytes, 1) + 255) & ~static_cast<size_t>(255);
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second < bytes) continue;
+    const size_t off = it->first, len = it->second;
+    free_.erase(it);
+    if (len > bytes) free_[off + bytes] = len - bytes;
+    allocated_[off] = bytes;
+    used_ += bytes;
+    return base_ + off;
+  }
+  return nullptr;
+}
+
+void Arena::release(void *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(mu_);
+  const size_t off = static_cast<size_t>(static_cast<char *>(p) - base_);
+  auto a = allocated_.find(off);
+  if (a == allocated_.end()) return;
+  size_t len = a->second;
+  allocated_.erase(a);
+  used_ -= len;
+  size_t start = off;
+  auto next = free_.lower_bound(off);
+  if (next != free_.end() && next->first == off + len) {
+    len += next->second;
+    next = free_.erase(next);
+  }
+  if (next != free_.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == start) {
+      start = prev->first;
+      len += prev->second;
+      free_.erase(prev);
+    }
+  }
+  free_[start] = len;
+}
+
+size_t Arena::largest_free() const {
+  std::lock_guard<std::mutex> g(mu_);
+  size_t m = 0;
+  for (auto &kv : free_) m = std::max(m, kv.second);
+  return m;
+}
+
+// ---------------------------------------------------------------- precompute
+namespace {
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+void split(double v, uint32_t *hi, uint32_t *lo) {
+  const float h = static_cast<float>(v);
+  const float l = static_cast<float>(v - static_cast<double>(h));
+  std::memcpy(hi, &h, 4);
+  std::memcpy(lo, &l, 4);
+}
+
+void put_f32(uint32_t *dst, double v) {
+  const float f = static_cast<float>(v);
+  std::memcpy(dst, &f, 4);
+}
+
+bool finite_f32(double v) {
+  return std::isfinite(v) && std::fabs(v) <= static_cast<double>(std::numeric_limits<float>::max());
+}
+
+double binom(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+}  // namespace
+
+zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volume) {
+  if (d.family > ZMC_POLY) return set_error(ZMC_EINVAL, "unknown family %u", d.family);
+  if (d.dim < 1 || d.dim > kMaxDim) return set_error(ZMC_EINVAL, "dim %u not in 1..7", d.dim);
+  if (d.n_samples == 0) return set_error(ZMC_EINVAL, "n_samples must be >= 1");
+  if (d.n_samples > (1ull << 62)) return set_error(ZMC_EINVAL, "n_samples too large");
+  if (d.family == ZMC_POLY && d.deg > 4) return set_error(ZMC_EINVAL, "poly degree %u > 4", d.deg);
+  const int dim = static_cast<int>(d.dim);
+  double w[kMaxDim] = {0};
+  double vol = 1.0;
+  for (int i = 0; i < dim; ++i) {
+    if (!std::isfinite(d.lo[i]) || !std::isfinite(d.hi[i]) || !(d.lo[i] < d.hi[i]))
+      return set_error(ZMC_EINVAL, "box dimension %d: need finite lo < hi", i);
+    w[i] = d.hi[i] - d.lo[i];
+    vol *= w[i];
+  }
+  for (int j = 0; j < ZMC_NPARAM; ++j)
+    if (!std::isfinite(d.p[j])) return set_error(ZMC_EINVAL, "parameter p[%d] not finite", j);
+
+  std::memset(fn, 0, sizeof(FnDev));
+  fn->variant = variant_code(d.family, d.dim, d.family == ZMC_POLY ? d.deg : 0);
+  fn->stream_id = d.stream_id;
+  fn->key0 = static_cast<uint32_t>(d.seed);
+  fn->key1 = static_cast<uint32_t>(d.seed >> 32);
+  fn->n_samples = d.n_samples;
+  fn->volume = vol;
+  const double *p = d.p;
+  bool ok = true;
+  switch (d.family) {
+    case ZMC_HARMONIC: {
+      // phase in turns = k.lo/(2 pi) + sum_i [k_i w_i / (2 pi)] m_i 2^-23
+      double phi = 0.0;
+      uint64_t *w64 = reinterpret_cast<uint64_t *>(fn->w);
+      for (int i = 0; i < dim; ++i) {
+        const double tau = p[2 + i] * w[i] / kTwoPi;
+        if (!(std::fabs(tau) <= 1048576.0))
+          return set_error(ZMC_EINVAL, "harmonic |k_i (hi_i-lo_i)| / 2pi above 2^20 turns");
+        const long long T = std::llround(std::ldexp(tau, 41));
+        w64[i] = static_cast<uint64_t>(T);
+        phi += p[2 + i] * d.lo[i] / kTwoPi;
+      }
+      if (!(std::fabs(phi) < 4.0e15)) return set_error(ZMC_EINVAL, "harmonic phase too large");
+      const double fr = phi - std::floor(phi);  // exact, in [0, 1)
+      w64[7] = static_cast<uint64_t>(std::ldexp(fr, 64));
+      ok = finite_f32(p[0]) && finite_f32(p[1]);
+      put_f32(&fn->w[16], p[0]);
+      put_f32(&fn->w[17], p[1]);
+      put_f32(&fn->w[18], -p[0]);
+      break;
+    }
+    case ZMC_ABSLIN: {
+      double C = 0.0;
+      for (int i = 0; i < dim; ++i) {
+        const double g = p[1 + i] * w[i];
+        ok = ok && finite_f32(g);
+        split(g, &fn->w[i], &fn->w[7 + i]);
+        C += p[1 + i] * (d.lo[i] - w[i]);
+      }
+      ok = ok && finite_f32(C) && finite_f32(p[0]);
+      split(C, &fn->w[14], &fn->w[15]);
+      put_f32(&fn->w[16], p[0]);
+      break;
+    }
+    case ZMC_GAUSS: {
+      const double sigma = p[1];
+      if (!(sigma > 0.0)) return set_error(ZMC_EINVAL, "gauss sigma must be > 0");
+      const double beta = std::sqrt(1.4426950408889634073599246810019 / 2.0) / sigma;
+      for (int i = 0; i < dim; ++i) {
+        const double h = w[i] * beta;
+        const double e = (d.lo[i] - w[i] - p[2 + i]) * beta;
+        ok = ok && finite_f32(h) && finite_f32(e);
+        split(h, &fn->w[i], &fn->w[7 + i]);
+        split(e, &fn->w[14 + i], &fn->w[21 + i]);
+      }
+      ok = ok && finite_f32(p[0]);
+      put_f32(&fn->w[28], p[0]);
+      break;
+    }
+    default: {  // POLY: q_i(u) = sum_j c_ij (lo_i + w_i u)^j = sum_k e_ik u^k
+      const int g = static_cast<int>(d.deg);
+      for (int i = 0; i < dim; ++i) {
+        for (int k = 0; k <= g; ++k) {
+          double e = 0.0;
+          for (int j = k; j <= g; ++j)
+            e += p[5 * i + j] * binom(j, k) * std::pow(d.lo[i], j - k) * std::pow(w[i], k);
+          ok = ok && finite_f32(e);
+          split(e, &fn->w[5 * i + k], &fn->w[35 + 5 * i + k]);
+        }
+      }
+      break;
+    }
+  }
+  if (!ok) return set_error(ZMC_EINVAL, "parameters out of FP32 range");
+  if (plain) {
+    std::memset(plain, 0, sizeof(PlainFn));
+    plain->family = d.family;
+    plain->dim = d.dim;
+    plain->stream_id = d.stream_id;
+    plain->deg = d.family == ZMC_POLY ? d.deg : 0;
+    plain->key0 = fn->key0;
+    plain->key1 = fn->key1;
+    plain->n_samples = d.n_samples;
+    for (int i = 0; i < dim; ++i) {
+      plain->lo[i] = d.lo[i];
+      plain->w[i] = w[i];
+    }
+    std::memcpy(plain->p, d.p, sizeof(d.p));
+  }
+  if (volume) *volume = vol;
+  return ZMC_OK;
+}
+
+zmc_status ensure_stage(zmc_ctx *ctx, size_t bytes) {
+  if (ctx->stage_bytes >= bytes) return ZMC_OK;
+  if (ctx->stage) {
+    ZMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFreeHost(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+  }
+  size_t want = std::max<size_t>(bytes, 1 << 20);
+  ZMC_CUDA(ctx, cudaHostAlloc(&ctx->stage, want, cudaHostAllocDefault));
+  ctx->stage_bytes = want;
+  return ZMC_OK;
+}
+
+unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items) {
+  const unsigned warps_per_block = ctx->shape.block / 32;
+  unsigned bps = ctx->shape.blocks_per_sm[family];
+  if (bps == 0 || bps > static_cast<unsigned>(ctx->max_blocks_per_sm[family]))
+    bps = static_cast<unsigned>(std::max(ctx->max_blocks_per_sm[family], 1));
+  const uint64_t full = static_cast<uint64_t>(ctx->sms) * bps;
+  const uint64_t need = (items + warps_per_block - 1) / warps_per_block;
+  return static_cast<unsigned>(std::max<uint64_t>(1, std::min(full, need)));
+}
+
+}  // namespace zmc
+
+using namespace zmc;
+
+// ---------------------------------------------------------------- plans
+struct zmc_plan {
+  zmc_ctx *ctx = nullptr;
+  size_t n = 0;
+  FnDev *d_fns = nullptr;
+  float2 *d_rec = nullptr;
+  zmc_result *d_out = nullptr;
+  Entry *d_entries = nullptr;
+  LaunchHdr *d_hdr = nullptr;
+  const FnDev **d_merge = nullptr;
+  std::vector<PlainFn> plain;
+  std::vector<double> volume;
+  double *d_prec = nullptr;
+  PlainJob *d_pjobs = nullptr;
+  std::vector<unsigned> pgrid;
+  std::vector<size_t> poff;
+  LaunchHdr h_hdr{};
+  uint64_t n_chunks = 0, n_samples = 0;
+  uint64_t fam_items[4] = {0, 0, 0, 0};
+  unsigned grid[4] = {0, 0, 0, 0};
+  cudaGraphExec_t graph = nullptr;
+  std::vector<void *> blocks;
+
+  void *alloc(size_t bytes) {
+    void *p = ctx->arena.alloc(bytes);
+    if (p) blocks.push_back(p);
+    return p;
+  }
+  void release_all() {
+    for (void *p : blocks) ctx->arena.release(p);
+    blocks.clear();
+  }
+};
+
+namespace {
+
+zmc_status check_ctx(zmc_ctx *ctx) {
+  if (!ctx) return set_error(ZMC_EINVAL, "null context");
+  if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");
+  return ZMC_OK;
+}
+
+zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out) {
+  if (!desc || !out || n == 0) return set_error(ZMC_EINVAL, "need n >= 1 descriptors");
+  if (n >= (1u << 31)) return set_error(ZMC_EINVAL, "too many descriptors");
+  auto plan = std::make_unique<zmc_plan>();
+  plan->ctx = ctx;
+  plan->n = n;
+  std::vector<FnDev> fns(n);
+  plan->plain.resize(n);
+  plan->volume.resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    zmc_status st = precompute(desc[i], &fns[i], &plan->plain[i], &plan->volume[i]);
+    if (st != ZMC_OK)
+      return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+  }
+  const uint64_t chunk = 128ull * ctx->quads_per_lane;
+  std::vector<uint64_t> nchunk(n), rec_off(n);
+  uint64_t total = 0, samples = 0;
+  for (size_t i = 0; i < n; ++i) {
+    nchunk[i] = (desc[i].n_samples + chunk - 1) / chunk;
+    rec_off[i] = total;
+    total += nchunk[i];
+    samples += desc[i].n_samples;
+  }
+  plan->n_chunks = total;
+  plan->n_samples = samples;
+
+  const size_t fn_bytes = n * sizeof(FnDev);
+  const size_t ent_bytes = n * sizeof(Entry);
+  const size_t mrg_bytes = n * sizeof(FnDev *);
+  plan->d_fns = static_cast<FnDev *>(plan->alloc(fn_bytes));
+  plan->d_rec = static_cast<float2 *>(plan->alloc(total * sizeof(float2)));
+  plan->d_out = static_cast<zmc_result *>(plan->alloc(n * sizeof(zmc_result)));
+  plan->d_entries = static_cast<Entry *>(plan->alloc(ent_bytes));
+  plan->d_merge = static_cast<const FnDev **>(plan->alloc(mrg_bytes));
+  plan->d_hdr = static_cast<LaunchHdr *>(plan->alloc(sizeof(LaunchHdr)));
+  if (!plan->d_fns || !plan->d_rec || !plan->d_out || !plan->d_entries || !plan->d_merge ||
+      !plan->d_hdr) {
+    plan->release_all();
+    return set_error(ZMC_ENOMEM, "plan needs %.1f MB of device memory; arena has %.1f MB free",
+                     (fn_bytes + total * 8.0 + n * 64.0) / 1e6,
+                     ctx->arena.largest_free() / 1e6);
+  }
+  for (size_t i = 0; i < n; ++i) {
+    fns[i].rec = plan->d_rec + rec_off[i];
+    fns[i].out = plan->d_out + i;
+  }
+  // item order: by family, then variant, then table order
+  std::vector<uint32_t> order(n);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+    const uint32_t fa = desc[a].family, fb = desc[b].family;
+    if (fa != fb) return fa < fb;
+    return fns[a].variant < fns[b].variant;
+  });
+  std::vector<Entry> ents(n);
+  LaunchHdr &h = plan->h_hdr;
+  std::memset(&h, 0, sizeof h);
+  uint64_t item = 0;
+  for (int f = 0; f < 4; ++f) h.item_begin[f] = h.item_end[f] = 0;
+  int cur_f = -1;
+  for (size_t k = 0; k < n; ++k) {
+    const uint32_t i = order[k];
+    const int f = static_cast<int>(desc[i].family);
+    while (cur_f < f) {
+      ++cur_f;
+      h.item_begin[cur_f] = item;
+      h.item_end[cur_f] = item;
+    }
+    ents[k].item_begin = item;
+    ents[k].fn = plan->d_fns + i;
+    ents[k].chunk_begin = 0;
+    item += nchunk[i];
+    h.item_end[f] = item;
+  }
+  while (cur_f < 3) {
+    ++cur_f;
+    h.item_begin[cur_f] = item;
+    h.item_end[cur_f] = item;
+  }
+  h.n_entries = static_cast<uint32_t>(n);
+  h.n_merge = static_cast<uint32_t>(n);
+  h.quads_per_lane = ctx->quads_per_lane;
+  for (int f = 0; f < 4; ++f) {
+    plan->fam_items[f] = h.item_end[f] - h.item_begin[f];
+    plan->grid[f] = family_grid(ctx, f, plan->fam_items[f]);
+  }
+  std::vector<const FnDev *> merge(n);
+  for (size_t i = 0; i < n; ++i) merge[i] = plan->d_fns + i;
+
+  const size_t stage = fn_bytes + ent_bytes + mrg_bytes + sizeof(LaunchHdr);
+  zmc_status st = ensure_stage(ctx, stage);
+  if (st != ZMC_OK) {
+    plan->release_all();
+    return st;
+  }
+  // the staging buffer is reused by the next call, so the copies are waited for
+  char *s = static_cast<char *>(ctx->stage);
+  std::memcpy(s, fns.data(), fn_bytes);
+  std::memcpy(s + fn_bytes, ents.data(), ent_bytes);
+  std::memcpy(s + fn_bytes + ent_bytes, merge.data(), mrg_bytes);
+  std::memcpy(s + fn_bytes + ent_bytes + mrg_bytes, &h, sizeof h);
+  cudaStream_t str = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(plan->d_fns, s, fn_bytes, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_entries, s + fn_bytes, ent_bytes, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_merge, s + fn_bytes + ent_bytes, mrg_bytes,
+                        cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_hdr, s + fn_bytes + ent_bytes + mrg_bytes, sizeof h,
+                        cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  if (e != cudaSuccess) {
+    plan->release_all();
+    return ctx_cuda_fail(ctx, e, "plan upload");
+  }
+  *out = plan.release();
+  return ZMC_OK;
+}
+
+zmc_status plan_enqueue(zmc_plan *plan, uint32_t stages) {
+  zmc_ctx *ctx = plan->ctx;
+  cudaStream_t str = ctx->stream;
+  if (stages & ZMC_STAGE_SAMPLE) {
+    ZMC_CUDA(ctx, cudaMemsetAsync(plan->d_hdr, 0, sizeof(plan->d_hdr->counter), str));
+    for (int f = 0; f < 4; ++f) {
+      if (plan->fam_items[f] == 0) continue;
+      ZMC_CUDA(ctx, launch_batched(f, plan->d_entries, plan->d_hdr, plan->grid[f],
+                                   ctx->shape.block, str));
+    }
+  }
+  if (stages & ZMC_STAGE_MERGE) {
+    const unsigned grid = static_cast<unsigned>(
+        std::min<size_t>((plan->n + 7) / 8, static_cast<size_t>(ctx->sms) * 16));
+    ZMC_CUDA(ctx, launch_merge(plan->d_merge, plan->d_hdr, grid, str));
+  }
+  return ZMC_OK;
+}
+
+zmc_status plan_results_to(zmc_plan *plan, zmc_result *out) {
+  zmc_ctx *ctx = plan->ctx;
+  const size_t bytes = plan->n * sizeof(zmc_result);
+  zmc_status st = ensure_stage(ctx, bytes);
+  if (st != ZMC_OK) return st;
+  ZMC_CUDA(ctx, cudaMemcpyAsync(ctx->stage, plan->d_out, bytes, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  ZMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::memcpy(out, ctx->stage, bytes);
+  return ZMC_OK;
+}
+
+void plan_free(zmc_plan *plan) {
+  if (!plan) return;
+  if (plan->graph) cudaGraphExecDestroy(plan->graph);
+  // stream order makes reuse of the released ranges safe for later work on this
+  // stream; wait anyway so no kernel of this plan can outlive the plan object.
+  cudaStreamSynchronize(plan->ctx->stream);
+  plan->release_all();
+  delete plan;
+}
+
+zmc_status plain_prepare(zmc_plan *plan) {
+  if (plan->d_pjobs) return ZMC_OK;
+  zmc_ctx *ctx = plan->ctx;
+  const size_t n = plan->n;
+  plan->pgrid.resize(n);
+  plan->poff.resize(n);
+  size_t total = 0;
+  for (size_t i = 0; i < n; ++i) {
+    plan->pgrid[i] = plain_grid(plan->plain[i], ctx->sms);
+    plan->poff[i] = total;
+    total += 3 * static_cast<size_t>(plan->pgrid[i]);
+  }
+  plan->d_prec = static_cast<double *>(plan->alloc(total * sizeof(double)));
+  PlainJob *jobs_dev = static_cast<PlainJob *>(plan->alloc(n * sizeof(PlainJob)));
+  if (!plan->d_prec || !jobs_dev) return set_error(ZMC_ENOMEM, "plain form: arena full");
+  std::vector<PlainJob> jobs(n);
+  for (size_t i = 0; i < n; ++i) {
+    jobs[i].rec = plan->d_prec + plan->poff[i];
+    jobs[i].nblk = plan->pgrid[i];
+    jobs[i].volume = plan->volume[i];
+    jobs[i].out = plan->d_out + i;
+  }
+  zmc_status st = ensure_stage(ctx, n * sizeof(PlainJob));
+  if (st != ZMC_OK) return st;
+  std::memcpy(ctx->stage, jobs.data(), n * sizeof(PlainJob));
+  ZMC_CUDA(ctx, cudaMemcpyAsync(jobs_dev, ctx->stage, n * sizeof(PlainJob),
+                                cudaMemcpyHostToDevice, ctx->stream));
+  ZMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  plan->d_pjobs = jobs_dev;
+  return ZMC_OK;
+}
+
+zmc_status plain_enqueue(zmc_plan *plan) {
+  zmc_ctx *ctx = plan->ctx;
+  zmc_status st = plain_prepare(plan);
+  if (st != ZMC_OK) return st;
+  for (size_t i = 0; i < plan->n; ++i)
+    ZMC_CUDA(ctx, launch_plain(plan->plain[i], plan->d_prec + plan->poff[i], plan->pgrid[i],
+                               ctx->stream));
+  ZMC_CUDA(ctx, launch_plain_merge(plan->d_pjobs, static_cast<uint32_t>(plan->n), ctx->stream));
+  return ZMC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+zmc_status zmc_default_options(zmc_options *opt) {
+  if (!opt) return set_error(ZMC_EINVAL, "null options");
+  std::memset(opt, 0, sizeof *opt);
+  opt->mem_budget_bytes = 1ull << 30;
+  opt->quads_per_lane = 16;
+  return ZMC_OK;
+}
+
+const char *zmc_last_error(zmc_ctx *) { return g_last_error.c_str(); }
+
+size_t zmc_desc_size(void) { return sizeof(zmc_desc); }
+
+zmc_status zmc_validate(const zmc_desc *desc, size_t n, size_t *bad_index) {
+  if (!desc && n) return set_error(ZMC_EINVAL, "null descriptor table");
+  FnDev fn;
+  for (size_t i = 0; i < n; ++i) {
+    zmc_status st = precompute(desc[i], &fn, nullptr, nullptr);
+    if (st != ZMC_OK) {
+      if (bad_index) *bad_index = i;
+      return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    }
+  }
+  return ZMC_OK;
+}
+size_t zmc_result_size(void) { return sizeof(zmc_result); }
+
+zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
+  if (!out) return set_error(ZMC_EINVAL, "null output pointer");
+  *out = nullptr;
+  zmc_options opt;
+  zmc_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.mem_budget_bytes == 0) opt.mem_budget_bytes = 1ull << 30;
+  if (opt.quads_per_lane == 0) opt.quads_per_lane = 16;
+  if (opt.quads_per_lane > 1024) return set_error(ZMC_EINVAL, "quads_per_lane above 1024");
+  if (opt.arena && (reinterpret_cast<uintptr_t>(opt.arena) & 255))
+    return set_error(ZMC_EINVAL, "arena must be 256-byte aligned");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0)
+    return set_error(ZMC_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  if (opt.device < 0 || opt.device >= ndev)
+    return set_error(ZMC_EINVAL, "device %d not present", opt.device);
+  auto ctx = std::make_unique<zmc_ctx>();
+  ctx->device = opt.device;
+  e = cudaSetDevice(opt.device);
+  if (e != cudaSuccess) return set_error(ZMC_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, opt.device);
+  if (e != cudaSuccess) return set_error(ZMC_ECUDA, "device query: %s", cudaGetErrorString(e));
+  ctx->sms = prop.multiProcessorCount;
+  ctx->gpu_name = prop.name;
+  if (opt.stream) {
+    ctx->stream = static_cast<cudaStream_t>(opt.stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return set_error(ZMC_ECUDA, "stream: %s", cudaGetErrorString(e));
+    ctx->own_stream = true;
+  }
+  if (opt.arena) {
+    ctx->arena_base = static_cast<char *>(opt.arena);
+  } else {
+    e = cudaMalloc(reinterpret_cast<void **>(&ctx->arena_base), opt.mem_budget_bytes);
+    if (e != cudaSuccess) {
+      if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+      return set_error(ZMC_ENOMEM, "arena of %llu bytes: %s",
+                       static_cast<unsigned long long>(opt.mem_budget_bytes),
+                       cudaGetErrorString(e));
+    }
+    ctx->own_arena = true;
+  }
+  ctx->arena.init(ctx->arena_base, opt.mem_budget_bytes);
+  ctx->quads_per_lane = opt.quads_per_lane;
+  ctx->max_chunks_per_iter = opt.max_chunks_per_iter;
+  ctx->autotune = opt.autotune != 0;
+  if (opt.tune_cache_path) ctx->tune_cache_path = opt.tune_cache_path;
+  for (int f = 0; f < 4; ++f) ctx->max_blocks_per_sm[f] = batched_max_blocks_per_sm(f, 256);
+  zmc_ctx *raw = ctx.release();
+  if (opt.serving) {
+    raw->serving = true;
+    zmc_status st = serving_start(raw);
+    if (st != ZMC_OK) {
+      zmc_destroy(raw);
+      return st;
+    }
+  }
+  *out = raw;
+  return ZMC_OK;
+}
+
+zmc_status zmc_destroy(zmc_ctx *ctx) {
+  if (!ctx) return ZMC_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->serving) serving_stop(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->stage) cudaFreeHost(ctx->stage);
+  if (ctx->own_arena && ctx->arena_base) cudaFree(ctx->arena_base);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return ZMC_OK;
+}
+
+zmc_status zmc_plan_create(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out) {
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  return plan_build(ctx, desc, n, out);
+}
+
+zmc_status zmc_plan_run(zmc_plan *plan, uint32_t stages) {
+  if (!plan) return set_error(ZMC_EINVAL, "null plan");
+  zmc_ctx *ctx = plan->ctx;
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  if ((stages & ZMC_STAGE_ALL) == 0 || (stages & ~ZMC_STAGE_ALL))
+    return set_error(ZMC_EINVAL, "stages must be a non-empty subset of ZMC_STAGE_ALL");
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  if (stages != ZMC_STAGE_ALL) return plan_enqueue(plan, stages);
+  if (!plan->graph) {
+    cudaGraph_t graph = nullptr;
+    ZMC_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    zmc_status est = plan_enqueue(plan, ZMC_STAGE_ALL);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (est != ZMC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return est;
+    }
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "graph capture");
+    e = cudaGraphInstantiate(&plan->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "graph instantiate");
+  }
+  ZMC_CUDA(ctx, cudaGraphLaunch(plan->graph, ctx->stream));
+  return ZMC_OK;
+}
+
+zmc_status zmc_plan_run_plain(zmc_plan *plan) {
+  if (!plan) return set_error(ZMC_EINVAL, "null plan");
+  zmc_status st = check_ctx(plan->ctx);
+  if (st != ZMC_OK) return st;
+  std::lock_guard<std::recursive_mutex> g(plan->ctx->api_mu);
+  return plain_enqueue(plan);
+}
+
+zmc_status zmc_plan_results(zmc_plan *plan, zmc_result *out) {
+  if (!plan || !out) return set_error(ZMC_EINVAL, "null argument");
+  zmc_status st = check_ctx(plan->ctx);
+  if (st != ZMC_OK) return st;
+  std::lock_guard<std::recursive_mutex> g(plan->ctx->api_mu);
+  return plan_results_to(plan, out);
+}
+
+zmc_status zmc_plan_device_results(zmc_plan *plan, void **device_ptr) {
+  if (!plan || !device_ptr) return set_error(ZMC_EINVAL, "null argument");
+  *device_ptr = plan->d_out;
+  return ZMC_OK;
+}
+
+zmc_status zmc_plan_info_get(const zmc_plan *plan, zmc_plan_info *out) {
+  if (!plan || !out) return set_error(ZMC_EINVAL, "null argument");
+  out->n_fn = plan->n;
+  out->n_chunks = plan->n_chunks;
+  out->n_samples = plan->n_samples;
+  unsigned g = 0;
+  for (int f = 0; f < 4; ++f) g = std::max(g, plan->grid[f]);
+  out->grid = g;
+  out->block = plan->ctx->shape.block;
+  out->quads_per_lane = plan->ctx->quads_per_lane;
+  out->sms = static_cast<uint32_t>(plan->ctx->sms);
+  return ZMC_OK;
+}
+
+zmc_status zmc_plan_destroy(zmc_plan *plan) {
+  if (!plan) return ZMC_OK;
+  std::lock_guard<std::recursive_mutex> g(plan->ctx->api_mu);
+  cudaSetDevice(plan->ctx->device);
+  plan_free(plan);
+  return ZMC_OK;
+}
+
+zmc_status zmc_integrate(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_result *out) {
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  if (!out) return set_error(ZMC_EINVAL, "null output");
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  zmc_plan *plan = nullptr;
+  st = plan_build(ctx, desc, n, &plan);
+  if (st != ZMC_OK) return st;
+  st = plan_enqueue(plan, ZMC_STAGE_ALL);
+  if (st == ZMC_OK) st = plan_results_to(plan, out);
+  plan_free(plan);
+  return st;
+}
+
+zmc_status zmc_integrate_plain(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_result *out) {
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  if (!out) return set_error(ZMC_EINVAL, "null output");
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  zmc_plan *plan = nullptr;
+  st = plan_build(ctx, desc, n, &plan);
+  if (st != ZMC_OK) return st;
+  st = plain_enqueue(plan);
+  if (st == ZMC_OK) st = plan_results_to(plan, out);
+  plan_free(plan);
+  return st;
+}
+
+zmc_status zmc_philox4x32_10(zmc_ctx *ctx, const uint32_t *ctr, const uint32_t *key,
+                             uint32_t *out, size_t n) {
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  if (n == 0) return ZMC_OK;
+  if (!ctr || !key || !out) return set_error(ZMC_EINVAL, "null argument");
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  const size_t bytes = n * 40;  // 16 ctr + 8 key + 16 out
+  char *d = static_cast<char *>(ctx->arena.alloc(bytes));
+  if (!d) return set_error(ZMC_ENOMEM, "arena full");
+  st = ensure_stage(ctx, bytes);
+  if (st == ZMC_OK) {
+    char *s = static_cast<char *>(ctx->stage);
+    std::memcpy(s, ctr, n * 16);
+    std::memcpy(s + n * 16, key, n * 8);
+    cudaError_t e = cudaMemcpyAsync(d, s, n * 24, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_philox(reinterpret_cast<uint32_t *>(d), reinterpret_cast<uint32_t *>(d + n * 16),
+                        reinterpret_cast<uint32_t *>(d + n * 24), n, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s, d + n * 24, n * 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+      st = ctx_cuda_fail(ctx, e, "philox");
+    else
+      std::memcpy(out, s, n * 16);
+  }
+  ctx->arena.release(d);
+  return st;
+}
+
+zmc_status zmc_eval_samples(zmc_ctx *ctx, const zmc_desc *desc, uint64_t s_begin,
+                            uint32_t count, float *out) {
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  if (!desc || !out) return set_error(ZMC_EINVAL, "null argument");
+  if (count == 0) return ZMC_OK;
+  if (s_begin + count > desc->n_samples)
+    return set_error(ZMC_EINVAL, "sample range beyond n_samples");
+  FnDev fn;
+  st = precompute(*desc, &fn, nullptr, nullptr);
+  if (st != ZMC_OK) return st;
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  const size_t bytes = sizeof(FnDev) + static_cast<size_t>(count) * 4;
+  char *d = static_cast<char *>(ctx->arena.alloc(bytes));
+  if (!d) return set_error(ZMC_ENOMEM, "arena full");
+  st = ensure_stage(ctx, bytes);
+  if (st == ZMC_OK) {
+    char *s = static_cast<char *>(ctx->stage);
+    std::memcpy(s, &fn, sizeof fn);
+    cudaError_t e = cudaMemcpyAsync(d, s, sizeof fn, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_eval(reinterpret_cast<FnDev *>(d), s_begin, count,
+                      reinterpret_cast<float *>(d + sizeof(FnDev)), ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s, d + sizeof(FnDev), static_cast<size_t>(count) * 4,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+      st = ctx_cuda_fail(ctx, e, "eval_samples");
+    else
+      std::memcpy(out, s, static_cast<size_t>(count) * 4);
+  }
+  ctx->arena.release(d);
+  return st;
+}
+
+}  // extern "C"

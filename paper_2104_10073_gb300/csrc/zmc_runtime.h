@@ -1,0 +1,96 @@
+// Host runtime internals shared by zmc_runtime.cpp (context, arena, plans) and
+// zmc_serving.cpp (continuous-batching scheduler).  Not part of the C ABI.
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "zmc_internal.h"
+
+namespace zmc {
+
+// Thread-local error text + status helper.
+zmc_status set_error(zmc_status st, const char *fmt, ...);
+
+// First-fit sub-allocator over one device buffer (256-byte granules, coalescing
+// free list).  All device memory a context uses comes from here.
+class Arena {
+ public:
+  void init(char *base, size_t bytes);
+  // nullptr when no free range is large enough.
+  void *alloc(size_t bytes);
+  void release(void *p);
+  size_t used() const { return used_; }
+  size_t size() const { return size_; }
+  size_t largest_free() const;
+
+ private:
+  char *base_ = nullptr;
+  size_t size_ = 0;
+  size_t used_ = 0;
+  std::map<size_t, size_t> free_;       // offset -> length
+  std::map<size_t, size_t> allocated_;  // offset -> length
+  mutable std::mutex mu_;
+};
+
+// Derived device form of one descriptor (validation + FP64 precompute).
+zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volume);
+
+// Launch-shape choice for the per-family persistent kernels.
+struct LaunchShape {
+  unsigned block = 256;
+  unsigned blocks_per_sm[4] = {0, 0, 0, 0};  // 0 -> occupancy maximum
+};
+
+struct Job;
+
+}  // namespace zmc
+
+struct zmc_plan;
+
+struct zmc_ctx {
+  int device = 0;
+  int sms = 0;
+  std::string gpu_name;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char *arena_base = nullptr;
+  bool own_arena = false;
+  zmc::Arena arena;
+  uint32_t quads_per_lane = 16;
+  uint32_t max_chunks_per_iter = 0;
+  bool autotune = false;
+  std::string tune_cache_path;
+  zmc::LaunchShape shape;
+  int max_blocks_per_sm[4] = {0, 0, 0, 0};
+  std::atomic<bool> poisoned{false};
+  std::recursive_mutex api_mu;  // serialises API calls that use the stream
+
+  // pinned staging for host <-> device copies of the blocking calls
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+
+  // serving
+  bool serving = false;
+  struct ServingState *srv = nullptr;  // owned; created by serving_start
+};
+
+namespace zmc {
+zmc_status ctx_cuda_fail(zmc_ctx *ctx, cudaError_t err, const char *what);
+zmc_status ensure_stage(zmc_ctx *ctx, size_t bytes);
+unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items);
+}  // namespace zmc
+
+// Serving state (zmc_serving.cpp).
+struct ServingState;
+zmc_status serving_start(zmc_ctx *ctx);
+void serving_stop(zmc_ctx *ctx);

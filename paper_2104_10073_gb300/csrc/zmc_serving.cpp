@@ -1,0 +1,556 @@
+// zmc_serving.cpp -- continuous batching of integration jobs.
+//
+// zmc_submit copies a job's descriptors, validates and precomputes them, and
+// queues the job.  A scheduler thread owns a stream and loops:
+//   1. admit queued jobs, in order, while their device block (descriptor table,
+//      one 8-byte record per chunk, result rows) fits in the arena;
+//   2. build one iteration: a fair share of at most max_chunks_per_iter chunks
+//      over all admitted jobs (every job with work left gets a share, so a small
+//      job that arrives behind a large one starts at the next iteration);
+//   3. upload the iteration's entry table and header, replay the iteration graph
+//      (per-family persistent sampling kernels + FP64 merge of every job whose
+//      last chunks ran), copy those jobs' results to pinned staging, record an
+//      event; two iteration slots are in flight at once;
+//   4. when a slot's event completes, hand the finished jobs' results to
+//      zmc_poll and free their device blocks.
+// A chunk's record depends only on (integrand, chunk) and the merge sums records
+// in a fixed order, so a job's results are bit-identical whether it runs alone or
+// mixed with others.  No kernel waits on another: every launch drains a finite
+// work list and exits.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "zmc_runtime.h"
+
+using namespace zmc;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum class JobState { kQueued, kRunning, kFinishing, kDone, kCancelled, kFailed };
+
+struct ServJob {
+  uint64_t id = 0;
+  size_t n = 0;
+  std::vector<FnDev> fns;      // host copy, device pointers filled at admission
+  std::vector<int> family;
+  std::vector<uint64_t> nchunk;
+  std::vector<uint64_t> next_chunk;
+  size_t cursor = 0;           // first integrand with chunks left to issue
+  uint64_t chunks_total = 0, chunks_issued = 0, samples = 0;
+  size_t block_bytes = 0;
+  char *dblock = nullptr;
+  FnDev *d_fns = nullptr;
+  zmc_result *d_out = nullptr;
+  JobState state = JobState::kQueued;
+  zmc_status fail_status = ZMC_OK;
+  std::vector<zmc_result> results;
+  uint64_t last_seq = 0;       // last iteration that touched the job
+  Clock::time_point t_submit, t_done;
+};
+
+struct Slot {
+  Entry *d_entries = nullptr;
+  LaunchHdr *d_hdr = nullptr;
+  const FnDev **d_merge = nullptr;
+  zmc_result *d_results = nullptr;  // contiguous copy target of merged results
+  char *h_stage = nullptr;          // pinned: entries | merge list | hdr | results
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool busy = false;
+  uint64_t seq = 0;
+  std::vector<std::shared_ptr<ServJob>> finishing;
+  std::vector<size_t> result_off;
+};
+
+}  // namespace
+
+struct ServingState {
+  zmc_ctx *ctx = nullptr;
+  std::thread thread;
+  std::mutex mu;
+  std::condition_variable cv_work;
+  std::condition_variable cv_done;
+  bool stop = false;
+  std::deque<std::shared_ptr<ServJob>> queue;
+  std::vector<std::shared_ptr<ServJob>> live;
+  std::deque<std::shared_ptr<ServJob>> to_merge;
+  std::unordered_map<uint64_t, std::shared_ptr<ServJob>> jobs;
+  std::vector<std::shared_ptr<ServJob>> cancelled_pending;
+  uint64_t next_id = 1;
+  cudaStream_t stream = nullptr;
+  Slot slots[2];
+  uint32_t max_chunks = 0;
+  uint32_t max_entries = 0;
+  uint32_t max_merge = 0;
+  unsigned grid[4] = {0, 0, 0, 0};
+  uint64_t seq = 0;
+  zmc_serving_stats stats{};
+  zmc_status thread_status = ZMC_OK;
+};
+
+namespace {
+
+size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+void free_job_device(ServingState *S, ServJob &j) {
+  if (j.dblock) {
+    S->ctx->arena.release(j.dblock);
+    j.dblock = nullptr;
+  }
+}
+
+// Admission: one arena block per job; upload its descriptor table.
+bool try_admit(ServingState *S, ServJob &j) {
+  zmc_ctx *ctx = S->ctx;
+  char *blk = static_cast<char *>(ctx->arena.alloc(j.block_bytes));
+  if (!blk) return false;
+  j.dblock = blk;
+  j.d_fns = reinterpret_cast<FnDev *>(blk);
+  size_t off = round256(j.n * sizeof(FnDev));
+  float2 *rec = reinterpret_cast<float2 *>(blk + off);
+  off += round256(j.chunks_total * sizeof(float2));
+  j.d_out = reinterpret_cast<zmc_result *>(blk + off);
+  uint64_t r = 0;
+  for (size_t i = 0; i < j.n; ++i) {
+    j.fns[i].rec = rec + r;
+    j.fns[i].out = j.d_out + i;
+    r += j.nchunk[i];
+  }
+  // pageable source: the copy completes before cudaMemcpyAsync returns
+  cudaError_t e = cudaMemcpyAsync(j.d_fns, j.fns.data(), j.n * sizeof(FnDev),
+                                  cudaMemcpyHostToDevice, S->stream);
+  if (e != cudaSuccess) {
+    ctx_cuda_fail(ctx, e, "serving admission upload");
+    S->thread_status = ZMC_ECUDA;
+  }
+  j.state = JobState::kRunning;
+  return true;
+}
+
+zmc_status build_slot_graph(ServingState *S, Slot &sl) {
+  zmc_ctx *ctx = S->ctx;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving capture");
+  cudaError_t le = cudaMemsetAsync(sl.d_hdr, 0, sizeof(sl.d_hdr->counter), S->stream);
+  for (int f = 0; f < 4 && le == cudaSuccess; ++f)
+    le = launch_batched(f, sl.d_entries, sl.d_hdr, S->grid[f], ctx->shape.block, S->stream);
+  if (le == cudaSuccess) {
+    const unsigned mg = static_cast<unsigned>(
+        std::min<uint64_t>((S->max_merge + 7) / 8, static_cast<uint64_t>(ctx->sms) * 16));
+    le = launch_merge(sl.d_merge, sl.d_hdr, mg, S->stream);
+  }
+  e = cudaStreamEndCapture(S->stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return ctx_cuda_fail(ctx, le, "serving capture launch");
+  }
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving end capture");
+  e = cudaGraphInstantiate(&sl.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving graph instantiate");
+  return ZMC_OK;
+}
+
+size_t stage_bytes(const ServingState *S) {
+  return round256(S->max_entries * sizeof(Entry)) + round256(S->max_merge * sizeof(FnDev *)) +
+         round256(sizeof(LaunchHdr)) + round256(S->max_merge * sizeof(zmc_result));
+}
+
+// Retire a completed slot: results to jobs, device blocks back to the arena.
+void retire_slot(ServingState *S, Slot &sl) {
+  std::lock_guard<std::mutex> g(S->mu);
+  const char *res_base = sl.h_stage + round256(S->max_entries * sizeof(Entry)) +
+                         round256(S->max_merge * sizeof(FnDev *)) +
+                         round256(sizeof(LaunchHdr));
+  const auto now = Clock::now();
+  for (size_t k = 0; k < sl.finishing.size(); ++k) {
+    auto &j = sl.finishing[k];
+    if (j->state == JobState::kFinishing) {
+      j->results.resize(j->n);
+      std::memcpy(j->results.data(), res_base + sl.result_off[k] * sizeof(zmc_result),
+                  j->n * sizeof(zmc_result));
+      j->state = JobState::kDone;
+      j->t_done = now;
+      S->stats.completed++;
+      S->stats.samples_done += j->samples;
+    }
+    free_job_device(S, *j);
+  }
+  sl.finishing.clear();
+  sl.result_off.clear();
+  sl.busy = false;
+  // cancelled jobs whose last iteration has now finished
+  auto &cp = S->cancelled_pending;
+  for (auto it = cp.begin(); it != cp.end();) {
+    if ((*it)->last_seq <= sl.seq) {
+      free_job_device(S, **it);
+      it = cp.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  S->cv_done.notify_all();
+}
+
+void scheduler_loop(ServingState *S) {
+  zmc_ctx *ctx = S->ctx;
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    // retire completed slots
+    for (auto &sl : S->slots) {
+      if (!sl.busy) continue;
+      cudaError_t q = cudaEventQuery(sl.ev);
+      if (q == cudaSuccess) {
+        retire_slot(S, sl);
+      } else if (q != cudaErrorNotReady) {
+        ctx_cuda_fail(ctx, q, "serving event");
+        S->thread_status = ZMC_ECUDA;
+      }
+    }
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->thread_status != ZMC_OK) {
+      // fail everything that is still pending
+      for (auto &kv : S->jobs)
+        if (kv.second->state != JobState::kDone && kv.second->state != JobState::kCancelled) {
+          kv.second->state = JobState::kFailed;
+          kv.second->fail_status = S->thread_status;
+        }
+      S->cv_done.notify_all();
+      if (S->stop) return;
+      S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+      continue;
+    }
+    // admission in arrival order
+    while (!S->queue.empty()) {
+      auto j = S->queue.front();
+      if (j->state == JobState::kCancelled) {
+        S->queue.pop_front();
+        continue;
+      }
+      if (!try_admit(S, *j)) break;
+      S->queue.pop_front();
+      S->live.push_back(j);
+    }
+    // pick a free slot
+    Slot *slot = nullptr;
+    for (auto &sl : S->slots)
+      if (!sl.busy) {
+        slot = &sl;
+        break;
+      }
+    const bool have_work = !S->live.empty() || !S->to_merge.empty();
+    if (!slot || !have_work) {
+      bool any_busy = S->slots[0].busy || S->slots[1].busy;
+      if (S->stop && !any_busy) return;
+      if (any_busy) {
+        lk.unlock();
+        // wait for the oldest busy slot outside the lock
+        Slot *oldest = nullptr;
+        for (auto &sl : S->slots)
+          if (sl.busy && (!oldest || sl.seq < oldest->seq)) oldest = &sl;
+        if (oldest) cudaEventSynchronize(oldest->ev);
+        continue;
+      }
+      if (!S->queue.empty()) {
+        // admission is blocked on memory that nothing in flight will free soon
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+        continue;
+      }
+      S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+      if (S->stop && S->queue.empty() && S->live.empty()) return;
+      continue;
+    }
+    // ---- build one iteration
+    const uint64_t seq = ++S->seq;
+    char *st = slot->h_stage;
+    Entry *ents = reinterpret_cast<Entry *>(st);
+    const FnDev **mrg =
+        reinterpret_cast<const FnDev **>(st + round256(S->max_entries * sizeof(Entry)));
+    LaunchHdr *hdr = reinterpret_cast<LaunchHdr *>(
+        st + round256(S->max_entries * sizeof(Entry)) + round256(S->max_merge * sizeof(FnDev *)));
+    std::vector<Entry> fam_ents[4];
+    uint64_t budget = S->max_chunks;
+    // fair share: equal split, leftovers handed out on further passes
+    std::vector<std::shared_ptr<ServJob>> active;
+    for (auto &j : S->live)
+      if (j->state == JobState::kRunning && j->chunks_issued < j->chunks_total) active.push_back(j);
+    uint32_t n_entries = 0;
+    while (budget > 0 && !active.empty() && n_entries < S->max_entries) {
+      const uint64_t share = std::max<uint64_t>(1, budget / active.size());
+      std::vector<std::shared_ptr<ServJob>> still;
+      for (auto &j : active) {
+        uint64_t take = std::min<uint64_t>(share, budget);
+        while (take > 0 && j->cursor < j->n && n_entries < S->max_entries) {
+          const size_t i = j->cursor;
+          const uint64_t left = j->nchunk[i] - j->next_chunk[i];
+          const uint64_t t = std::min(left, take);
+          Entry en;
+          en.item_begin = 0;  // filled when families are concatenated
+          en.fn = j->d_fns + i;
+          en.chunk_begin = j->next_chunk[i];
+          fam_ents[j->family[i]].push_back(en);
+          // remember the run length in item_begin for now
+          fam_ents[j->family[i]].back().item_begin = t;
+          ++n_entries;
+          j->next_chunk[i] += t;
+          j->chunks_issued += t;
+          take -= t;
+          budget -= t;
+          if (j->next_chunk[i] == j->nchunk[i]) ++j->cursor;
+        }
+        j->last_seq = seq;
+        if (j->chunks_issued == j->chunks_total)
+          S->to_merge.push_back(j);
+        else
+          still.push_back(j);
+        if (budget == 0) break;
+      }
+      active.swap(still);
+    }
+    // concatenate by family; convert run lengths into item offsets
+    std::memset(hdr, 0, sizeof *hdr);
+    uint64_t item = 0;
+    uint32_t k = 0;
+    for (int f = 0; f < 4; ++f) {
+      hdr->item_begin[f] = item;
+      for (auto &en : fam_ents[f]) {
+        const uint64_t len = en.item_begin;
+        en.item_begin = item;
+        ents[k++] = en;
+        item += len;
+      }
+      hdr->item_end[f] = item;
+    }
+    hdr->n_entries = k;
+    hdr->quads_per_lane = ctx->quads_per_lane;
+    // merge list: whole jobs whose chunks have all been issued
+    uint32_t nm = 0;
+    slot->finishing.clear();
+    slot->result_off.clear();
+    while (!S->to_merge.empty()) {
+      auto j = S->to_merge.front();
+      if (j->state != JobState::kRunning) {
+        S->to_merge.pop_front();
+        continue;
+      }
+      if (nm + j->n > S->max_merge) break;
+      for (size_t i = 0; i < j->n; ++i) mrg[nm + i] = j->d_fns + i;
+      slot->finishing.push_back(j);
+      slot->result_off.push_back(nm);
+      nm += static_cast<uint32_t>(j->n);
+      j->state = JobState::kFinishing;
+      j->last_seq = seq;
+      S->to_merge.pop_front();
+    }
+    hdr->n_merge = nm;
+    // drop finished jobs from the live list
+    S->live.erase(std::remove_if(S->live.begin(), S->live.end(),
+                                 [](const std::shared_ptr<ServJob> &j) {
+                                   return j->state != JobState::kRunning ||
+                                          j->chunks_issued == j->chunks_total;
+                                 }),
+                  S->live.end());
+    S->stats.iterations++;
+    lk.unlock();
+
+    // ---- enqueue: upload tables, replay the graph, copy merged results back
+    const size_t ent_bytes = round256(S->max_entries * sizeof(Entry));
+    const size_t mrg_bytes = round256(S->max_merge * sizeof(FnDev *));
+    const size_t hdr_bytes = round256(sizeof(LaunchHdr));
+    cudaError_t e = cudaSuccess;
+    if (k > 0)
+      e = cudaMemcpyAsync(slot->d_entries, ents, k * sizeof(Entry), cudaMemcpyHostToDevice,
+                          S->stream);
+    if (e == cudaSuccess && nm > 0)
+      e = cudaMemcpyAsync(slot->d_merge, mrg, nm * sizeof(FnDev *), cudaMemcpyHostToDevice,
+                          S->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(slot->d_hdr, hdr, sizeof(LaunchHdr), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(slot->graph, S->stream);
+    char *res_stage = st + ent_bytes + mrg_bytes + hdr_bytes;
+    for (size_t q = 0; e == cudaSuccess && q < slot->finishing.size(); ++q) {
+      auto &j = slot->finishing[q];
+      e = cudaMemcpyAsync(res_stage + slot->result_off[q] * sizeof(zmc_result), j->d_out,
+                          j->n * sizeof(zmc_result), cudaMemcpyDeviceToHost, S->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(slot->ev, S->stream);
+    if (e != cudaSuccess) {
+      ctx_cuda_fail(ctx, e, "serving iteration");
+      S->thread_status = ZMC_ECUDA;
+      continue;
+    }
+    slot->busy = true;
+    slot->seq = seq;
+  }
+}
+
+}  // namespace
+
+zmc_status serving_start(zmc_ctx *ctx) {
+  auto S = std::make_unique<ServingState>();
+  S->ctx = ctx;
+  S->max_chunks = ctx->max_chunks_per_iter ? ctx->max_chunks_per_iter : (1u << 18);
+  S->max_entries = std::max<uint32_t>(S->max_chunks, 1024);
+  S->max_entries = std::min<uint32_t>(S->max_entries, 1u << 20);
+  S->max_merge = 1u << 16;
+  cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving stream");
+  for (int f = 0; f < 4; ++f) S->grid[f] = family_grid(ctx, f, ~0ull >> 8);
+  const size_t sb = stage_bytes(S.get());
+  for (auto &sl : S->slots) {
+    sl.d_entries = static_cast<Entry *>(ctx->arena.alloc(S->max_entries * sizeof(Entry)));
+    sl.d_merge = static_cast<const FnDev **>(ctx->arena.alloc(S->max_merge * sizeof(FnDev *)));
+    sl.d_hdr = static_cast<LaunchHdr *>(ctx->arena.alloc(sizeof(LaunchHdr)));
+    if (!sl.d_entries || !sl.d_merge || !sl.d_hdr)
+      return set_error(ZMC_ENOMEM, "serving tables do not fit the arena");
+    e = cudaHostAlloc(reinterpret_cast<void **>(&sl.h_stage), sb, cudaHostAllocDefault);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving staging");
+    e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving event");
+    zmc_status st = build_slot_graph(S.get(), sl);
+    if (st != ZMC_OK) return st;
+  }
+  S->stats.arena_bytes = ctx->arena.size();
+  ServingState *raw = S.release();
+  ctx->srv = raw;
+  raw->thread = std::thread(scheduler_loop, raw);
+  return ZMC_OK;
+}
+
+void serving_stop(zmc_ctx *ctx) {
+  ServingState *S = ctx->srv;
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->stop = true;
+    for (auto &j : S->queue) j->state = JobState::kCancelled;
+    S->queue.clear();
+    for (auto &j : S->live) j->state = JobState::kCancelled;
+    S->live.clear();
+    S->to_merge.clear();
+  }
+  S->cv_work.notify_all();
+  if (S->thread.joinable()) S->thread.join();
+  cudaStreamSynchronize(S->stream);
+  for (auto &kv : S->jobs) free_job_device(S, *kv.second);
+  for (auto &sl : S->slots) {
+    if (sl.graph) cudaGraphExecDestroy(sl.graph);
+    if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.h_stage) cudaFreeHost(sl.h_stage);
+    ctx->arena.release(sl.d_entries);
+    ctx->arena.release(sl.d_merge);
+    ctx->arena.release(sl.d_hdr);
+  }
+  cudaStreamDestroy(S->stream);
+  delete S;
+  ctx->srv = nullptr;
+}
+
+extern "C" {
+
+zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *job_id) {
+  if (!ctx || !desc || !job_id || n == 0) return set_error(ZMC_EINVAL, "bad submit arguments");
+  if (!ctx->serving || !ctx->srv) return set_error(ZMC_EINVAL, "context created without serving");
+  if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
+  ServingState *S = ctx->srv;
+  auto j = std::make_shared<ServJob>();
+  j->n = n;
+  j->fns.resize(n);
+  j->family.resize(n);
+  j->nchunk.resize(n);
+  j->next_chunk.assign(n, 0);
+  const uint64_t chunk = 128ull * ctx->quads_per_lane;
+  for (size_t i = 0; i < n; ++i) {
+    zmc_status st = precompute(desc[i], &j->fns[i], nullptr, nullptr);
+    if (st != ZMC_OK) return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    j->family[i] = static_cast<int>(desc[i].family);
+    j->nchunk[i] = (desc[i].n_samples + chunk - 1) / chunk;
+    j->chunks_total += j->nchunk[i];
+    j->samples += desc[i].n_samples;
+  }
+  j->block_bytes = round256(n * sizeof(FnDev)) + round256(j->chunks_total * sizeof(float2)) +
+                   round256(n * sizeof(zmc_result));
+  if (n > S->max_merge)
+    return set_error(ZMC_EINVAL, "a job may hold at most %u integrands", S->max_merge);
+  if (j->block_bytes > ctx->arena.size())
+    return set_error(ZMC_ENOMEM, "job needs %zu bytes; the arena has %zu", j->block_bytes,
+                     ctx->arena.size());
+  j->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->stop) return set_error(ZMC_ECLOSED, "context is shutting down");
+    j->id = S->next_id++;
+    S->jobs[j->id] = j;
+    S->queue.push_back(j);
+    S->stats.submitted++;
+    *job_id = j->id;
+  }
+  S->cv_work.notify_one();
+  return ZMC_OK;
+}
+
+zmc_status zmc_poll(zmc_ctx *ctx, uint64_t job_id, zmc_result *out, int32_t wait_ms) {
+  if (!ctx || !ctx->srv) return set_error(ZMC_EINVAL, "context created without serving");
+  ServingState *S = ctx->srv;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(job_id);
+  if (it == S->jobs.end()) return set_error(ZMC_ENOTFOUND, "unknown job %llu",
+                                            static_cast<unsigned long long>(job_id));
+  std::shared_ptr<ServJob> j = it->second;
+  auto finished = [&] {
+    return j->state == JobState::kDone || j->state == JobState::kCancelled ||
+           j->state == JobState::kFailed;
+  };
+  if (!finished()) {
+    if (wait_ms == 0) return set_error(ZMC_EAGAIN, "job not finished");
+    if (wait_ms < 0) {
+      S->cv_done.wait(lk, finished);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), finished)) {
+      return set_error(ZMC_ETIMEOUT, "job not finished after %d ms", wait_ms);
+    }
+  }
+  S->jobs.erase(job_id);
+  if (j->state == JobState::kCancelled) return set_error(ZMC_ECLOSED, "job was cancelled");
+  if (j->state == JobState::kFailed) return set_error(j->fail_status, "job failed");
+  if (out) std::memcpy(out, j->results.data(), j->n * sizeof(zmc_result));
+  return ZMC_OK;
+}
+
+zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id) {
+  if (!ctx || !ctx->srv) return set_error(ZMC_EINVAL, "context created without serving");
+  ServingState *S = ctx->srv;
+  std::lock_guard<std::mutex> g(S->mu);
+  auto it = S->jobs.find(job_id);
+  if (it == S->jobs.end()) return set_error(ZMC_ENOTFOUND, "unknown job");
+  auto &j = it->second;
+  if (j->state == JobState::kDone || j->state == JobState::kFailed) return ZMC_OK;
+  if (j->state == JobState::kQueued) {
+    j->state = JobState::kCancelled;
+  } else if (j->state == JobState::kRunning || j->state == JobState::kFinishing) {
+    j->state = JobState::kCancelled;
+    // device memory is freed once the last iteration that used it has finished
+    S->cancelled_pending.push_back(j);
+    S->live.erase(std::remove(S->live.begin(), S->live.end(), j), S->live.end());
+  }
+  S->stats.cancelled++;
+  S->cv_done.notify_all();
+  return ZMC_OK;
+}
+
+zmc_status zmc_serving_stats_get(zmc_ctx *ctx, zmc_serving_stats *out) {
+  if (!ctx || !ctx->srv || !out) return set_error(ZMC_EINVAL, "no serving state");
+  ServingState *S = ctx->srv;
+  std::lock_guard<std::mutex> g(S->mu);
+  *out = S->stats;
+  out->queued = S->queue.size();
+  out->running = S->live.size();
+  out->arena_used_bytes = ctx->arena.used();
+  out->arena_bytes = ctx->arena.size();
+  return ZMC_OK;
+}
+
+}  // extern "C"

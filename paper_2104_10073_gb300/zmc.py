@@ -1,0 +1,307 @@
+"""ctypes binding of ``libzmc.so`` (C ABI declared in ``include/zmc.h``).
+
+Argument marshalling only: every step of the integration runs in the library's
+CUDA kernels.  Function names are the C entry points'.  Descriptor tables are
+numpy structured arrays with the ``zmc_desc`` layout
+(:data:`paper_2104_10073_gb300.workloads.DESC_DTYPE`), passed by pointer.
+
+There is no fallback: if the library cannot be loaded, :func:`lib` raises.
+PyTorch is used only to provide device memory (an optional arena tensor) and
+the CUDA stream the library runs on (see :class:`Context`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzmc.so")
+
+# zmc_status
+ZMC_OK, ZMC_EINVAL, ZMC_ENOMEM, ZMC_EAGAIN, ZMC_ETIMEOUT = 0, 1, 2, 3, 4
+ZMC_ECUDA, ZMC_ENOTFOUND, ZMC_ECLOSED, ZMC_ENOSYS = 5, 6, 7, 8
+STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_EAGAIN",
+                4: "ZMC_ETIMEOUT", 5: "ZMC_ECUDA", 6: "ZMC_ENOTFOUND", 7: "ZMC_ECLOSED",
+                8: "ZMC_ENOSYS"}
+ZMC_STAGE_SAMPLE, ZMC_STAGE_MERGE, ZMC_STAGE_ALL = 1, 2, 3
+
+RESULT_DTYPE = np.dtype([("estimate", "<f8"), ("stderr", "<f8"), ("n", "<u8"),
+                         ("status", "<i4"), ("reserved", "<i4")])
+assert RESULT_DTYPE.itemsize == 32
+
+
+class zmc_options(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("arena", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p), ("max_chunks_per_iter", ctypes.c_uint32),
+                ("autotune", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("quads_per_lane", ctypes.c_uint32), ("tune_cache_path", ctypes.c_char_p),
+                ("serving", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class zmc_plan_info(ctypes.Structure):
+    _fields_ = [("n_fn", ctypes.c_uint64), ("n_chunks", ctypes.c_uint64),
+                ("n_samples", ctypes.c_uint64), ("grid", ctypes.c_uint32),
+                ("block", ctypes.c_uint32), ("quads_per_lane", ctypes.c_uint32),
+                ("sms", ctypes.c_uint32)]
+
+
+class zmc_serving_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "completed", "cancelled", "queued", "running", "iterations",
+        "samples_done", "arena_used_bytes", "arena_bytes")]
+
+
+class ZmcError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "zmc_default_options": ([ctypes.POINTER(zmc_options)], ctypes.c_int),
+    "zmc_create": ([ctypes.POINTER(zmc_options), ctypes.POINTER(_P)], ctypes.c_int),
+    "zmc_destroy": ([_P], ctypes.c_int),
+    "zmc_last_error": ([_P], ctypes.c_char_p),
+    "zmc_integrate": ([_P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "zmc_integrate_plain": ([_P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "zmc_submit": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "zmc_poll": ([_P, ctypes.c_uint64, _P, ctypes.c_int32], ctypes.c_int),
+    "zmc_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "zmc_serving_stats_get": ([_P, ctypes.POINTER(zmc_serving_stats)], ctypes.c_int),
+    "zmc_plan_create": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)], ctypes.c_int),
+    "zmc_plan_run": ([_P, ctypes.c_uint32], ctypes.c_int),
+    "zmc_plan_run_plain": ([_P], ctypes.c_int),
+    "zmc_plan_results": ([_P, _P], ctypes.c_int),
+    "zmc_plan_device_results": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
+    "zmc_plan_info_get": ([_P, ctypes.POINTER(zmc_plan_info)], ctypes.c_int),
+    "zmc_plan_destroy": ([_P], ctypes.c_int),
+    "zmc_philox4x32_10": ([_P, _P, _P, _P, ctypes.c_size_t], ctypes.c_int),
+    "zmc_eval_samples": ([_P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
+    "zmc_validate": ([_P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "zmc_desc_size": ([], ctypes.c_size_t),
+    "zmc_result_size": ([], ctypes.c_size_t),
+}
+EXPORTED = tuple(_SIGS)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libzmc.so`` (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} not built; run paper_2104_10073_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            if L.zmc_desc_size() != W.DESC_DTYPE.itemsize:
+                raise RuntimeError("zmc_desc layout mismatch")
+            if L.zmc_result_size() != RESULT_DTYPE.itemsize:
+                raise RuntimeError("zmc_result layout mismatch")
+            _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != ZMC_OK:
+        raise ZmcError(status, where, lib().zmc_last_error(None).decode())
+
+
+def _table(desc) -> np.ndarray:
+    t = np.ascontiguousarray(desc, dtype=W.DESC_DTYPE)
+    if t.ndim != 1:
+        t = t.reshape(-1)
+    return t
+
+
+# ------------------------------------------------------------------ thin wrappers
+def zmc_default_options() -> zmc_options:
+    o = zmc_options()
+    _check(lib().zmc_default_options(ctypes.byref(o)), "zmc_default_options")
+    return o
+
+
+def zmc_create(opt: zmc_options | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().zmc_create(ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)),
+           "zmc_create")
+    return h.value
+
+
+def zmc_destroy(ctx: int) -> None:
+    _check(lib().zmc_destroy(ctx), "zmc_destroy")
+
+
+def zmc_last_error(ctx: int | None = None) -> str:
+    return lib().zmc_last_error(ctx).decode()
+
+
+def zmc_integrate(ctx: int, desc) -> np.ndarray:
+    t = _table(desc)
+    out = np.zeros(len(t), dtype=RESULT_DTYPE)
+    _check(lib().zmc_integrate(ctx, t.ctypes.data, len(t), out.ctypes.data), "zmc_integrate")
+    return out
+
+
+def zmc_integrate_plain(ctx: int, desc) -> np.ndarray:
+    t = _table(desc)
+    out = np.zeros(len(t), dtype=RESULT_DTYPE)
+    _check(lib().zmc_integrate_plain(ctx, t.ctypes.data, len(t), out.ctypes.data),
+           "zmc_integrate_plain")
+    return out
+
+
+def zmc_submit(ctx: int, desc) -> int:
+    t = _table(desc)
+    jid = ctypes.c_uint64()
+    _check(lib().zmc_submit(ctx, t.ctypes.data, len(t), ctypes.byref(jid)), "zmc_submit")
+    return jid.value
+
+
+def zmc_poll(ctx: int, job_id: int, n: int, wait_ms: int = -1):
+    """Returns (status, results-or-None); ZMC_EAGAIN / ZMC_ETIMEOUT are not errors."""
+    out = np.zeros(n, dtype=RESULT_DTYPE)
+    st = lib().zmc_poll(ctx, job_id, out.ctypes.data, wait_ms)
+    if st in (ZMC_EAGAIN, ZMC_ETIMEOUT):
+        return st, None
+    if st == ZMC_OK:
+        return st, out
+    return st, None
+
+
+def zmc_cancel(ctx: int, job_id: int) -> None:
+    _check(lib().zmc_cancel(ctx, job_id), "zmc_cancel")
+
+
+def zmc_serving_stats_get(ctx: int) -> dict:
+    s = zmc_serving_stats()
+    _check(lib().zmc_serving_stats_get(ctx, ctypes.byref(s)), "zmc_serving_stats_get")
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+def zmc_plan_create(ctx: int, desc) -> int:
+    t = _table(desc)
+    h = ctypes.c_void_p()
+    _check(lib().zmc_plan_create(ctx, t.ctypes.data, len(t), ctypes.byref(h)),
+           "zmc_plan_create")
+    return h.value
+
+
+def zmc_plan_run(plan: int, stages: int = ZMC_STAGE_ALL) -> None:
+    _check(lib().zmc_plan_run(plan, stages), "zmc_plan_run")
+
+
+def zmc_plan_run_plain(plan: int) -> None:
+    _check(lib().zmc_plan_run_plain(plan), "zmc_plan_run_plain")
+
+
+def zmc_plan_results(plan: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=RESULT_DTYPE)
+    _check(lib().zmc_plan_results(plan, out.ctypes.data), "zmc_plan_results")
+    return out
+
+
+def zmc_plan_device_results(plan: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().zmc_plan_device_results(plan, ctypes.byref(p)), "zmc_plan_device_results")
+    return p.value
+
+
+def zmc_plan_info_get(plan: int) -> dict:
+    i = zmc_plan_info()
+    _check(lib().zmc_plan_info_get(plan, ctypes.byref(i)), "zmc_plan_info_get")
+    return {name: getattr(i, name) for name, _ in i._fields_}
+
+
+def zmc_plan_destroy(plan: int) -> None:
+    _check(lib().zmc_plan_destroy(plan), "zmc_plan_destroy")
+
+
+def zmc_philox4x32_10(ctx: int, ctr, key) -> np.ndarray:
+    ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    out = np.zeros_like(ctr)
+    _check(lib().zmc_philox4x32_10(ctx, ctr.ctypes.data, key.ctypes.data, out.ctypes.data,
+                                   ctr.shape[0]), "zmc_philox4x32_10")
+    return out
+
+
+def zmc_eval_samples(ctx: int, row, s_begin: int, count: int) -> np.ndarray:
+    t = _table(np.asarray(row).reshape(1))
+    out = np.zeros(count, dtype=np.float32)
+    _check(lib().zmc_eval_samples(ctx, t.ctypes.data, int(s_begin), int(count),
+                                  out.ctypes.data), "zmc_eval_samples")
+    return out
+
+
+def zmc_validate(desc):
+    """(status, first bad row or None, message); host only."""
+    t = _table(desc)
+    bad = ctypes.c_size_t(0)
+    st = lib().zmc_validate(t.ctypes.data, len(t), ctypes.byref(bad))
+    if st == ZMC_OK:
+        return st, None, ""
+    return st, bad.value, zmc_last_error()
+
+
+# ------------------------------------------------------------------ convenience
+class Context:
+    """A library context whose device memory and stream come from PyTorch.
+
+    ``arena_bytes`` of device memory are taken from PyTorch's caching allocator
+    (one uint8 tensor kept alive by this object) and the library runs on
+    ``stream`` (default: a new ``torch.cuda.Stream``).
+    """
+
+    def __init__(self, arena_bytes: int = 1 << 30, device: int = 0, stream=None,
+                 serving: bool = False, quads_per_lane: int = 16, max_chunks_per_iter: int = 0,
+                 use_torch_memory: bool = True):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        opt = zmc_default_options()
+        opt.mem_budget_bytes = arena_bytes
+        opt.device = device
+        opt.stream = self.stream.cuda_stream
+        opt.serving = 1 if serving else 0
+        opt.quads_per_lane = quads_per_lane
+        opt.max_chunks_per_iter = max_chunks_per_iter
+        self.arena = None
+        if use_torch_memory:
+            self.arena = torch.empty(arena_bytes + 256, dtype=torch.uint8,
+                                     device=f"cuda:{device}")
+            base = self.arena.data_ptr()
+            opt.arena = (base + 255) & ~255
+        self.handle = zmc_create(opt)
+
+    def close(self):
+        if self.handle:
+            zmc_destroy(self.handle)
+            self.handle = None
+            self.arena = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -33,3 +33,38 @@ def torch_philox(tmp_path_factory):
                         dtype=np.uint32).reshape(-1, 4)
 
     return run
+
+
+@pytest.fixture(scope="session")
+def zctx():
+    """A library context on cuda:0 (device memory and stream from PyTorch)."""
+    import torch
+
+    from paper_2104_10073_gb300 import build, zmc
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    ctx = zmc.Context(arena_bytes=4 << 30)
+    yield ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="session")
+def curand_philox(tmp_path_factory):
+    """Callable (ctr (n,4), key (n,2)) -> words, backed by cuRAND's device Philox."""
+    import numpy as np
+
+    exe = str(tmp_path_factory.mktemp("cpd") / "curand_philox_dump")
+    src = os.path.join(ROOT, "tests", "helpers", "curand_philox_dump.cu")
+    nvcc = "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", src, "-o", exe],
+                   check=True)
+
+    def run(ctr, key):
+        lines = [" ".join(str(int(v)) for v in list(c) + list(k)) for c, k in zip(ctr, key)]
+        out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True,
+                             text=True, check=True)
+        return np.array([[int(v) for v in ln.split()] for ln in out.stdout.splitlines()],
+                        dtype=np.uint32).reshape(-1, 4)
+
+    return run

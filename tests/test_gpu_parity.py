@@ -1,0 +1,266 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on identical samples.
+
+Tolerances are stated in tests/gpu_common.py.  Sizes span many chunks and
+ragged tails (chunk = 128 * quads_per_lane = 2048 samples by default); the
+full-size mixed table runs in the benchmark's launch configuration and is
+checked on sampled rows the oracle computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_10073_gb300 import workloads as W
+from paper_2104_10073_gb300 import zmc
+from tests import closed_forms as CF
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+EDGE_SIZES = [1, 2, 3, 4, 5, 7, 8, 127, 128, 129, 2047, 2048, 2049, 4095, 4096, 4097, 10003,
+              65537]
+
+
+# ------------------------------------------------------------------ generator
+def test_philox_bitexact_vs_oracle(zctx):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(5000, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(5000, 2), dtype=np.uint64).astype(np.uint32)
+    edge = np.array([[0, 0, 0, 0], [2**32 - 1] * 4, [2**32 - 1, 0, 0, 0], [0, 2**32 - 1, 5, 0]],
+                    dtype=np.uint32)
+    ctr = np.concatenate([ctr, edge])
+    key = np.concatenate([key, np.array([[0, 0], [2**32 - 1] * 2, [1, 0], [0, 1]],
+                                        dtype=np.uint32)])
+    got = zmc.zmc_philox4x32_10(zctx.handle, ctr, key)
+    want = oracle.philox4x32_10(ctr, key)
+    assert np.array_equal(got, want)
+
+
+def test_philox_three_way_with_curand(zctx, curand_philox):
+    """Library, oracle and cuRAND's device Philox4x32-10 agree bit for bit."""
+    rng = np.random.default_rng(2)
+    ctr = rng.integers(0, 2**32, size=(2000, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(2000, 2), dtype=np.uint64).astype(np.uint32)
+    cur = curand_philox(ctr, key)
+    assert np.array_equal(cur, oracle.philox4x32_10(ctr, key))
+    assert np.array_equal(cur, zmc.zmc_philox4x32_10(zctx.handle, ctr, key))
+
+
+# ------------------------------------------------------------------ per sample
+def _per_sample_rows():
+    rng = np.random.default_rng(7)
+    rows = []
+    for fam in range(4):
+        for d in range(1, 8):
+            t = W.random_table(1, rng, n_lo=10**6, n_hi=10**6, families=[fam], dims=[d],
+                               seed=int(rng.integers(0, 2**63)))
+            t[0]["stream_id"] = int(rng.integers(0, 2**32))
+            rows.append(t[0])
+    # large phases: |k.x| up to ~420 rad
+    t = W.empty(1)
+    W.harmonic(t[0], 1.1, -0.8, [30.0] * 7, [-1.0] * 7, [1.0] * 7, 10**6, seed=3)
+    rows.append(t[0])
+    return rows
+
+
+def test_eval_samples_match_oracle_per_sample(zctx):
+    for row in _per_sample_rows():
+        for s0 in (0, 1, 999_000):
+            count = 997
+            got = zmc.zmc_eval_samples(zctx.handle, row, s0, count).astype(np.float64)
+            _, _, want = oracle.samples(row, s0, count)
+            tol = 4e-6 * G.sample_scale(row)
+            err = np.max(np.abs(got - want))
+            assert err <= tol, (int(row["family"]), int(row["dim"]), s0, err, tol)
+
+
+def test_eval_samples_across_block_index_carry(zctx):
+    """Samples whose Philox block index crosses 2^32 (counter word 1 carries)."""
+    for d in (1, 3, 7):
+        t = W.empty(1)
+        W.abslin(t[0], 1.0, [1.0] * d, [0.0] * d, [1.0] * d, 2**36, seed=9, stream_id=4)
+        s0 = (4 * 2**32) // d - 40
+        got = zmc.zmc_eval_samples(zctx.handle, t[0], s0, 80).astype(np.float64)
+        _, _, want = oracle.samples(t[0], s0, 80)
+        assert np.max(np.abs(got - want)) <= 4e-6 * G.sample_scale(t[0])
+
+
+# ------------------------------------------------------------------ estimates
+@pytest.mark.parametrize("fam", [W.HARMONIC, W.ABSLIN, W.GAUSS, W.POLY])
+def test_integrate_edge_sizes_every_dim(zctx, fam):
+    rng = np.random.default_rng(100 + fam)
+    rows = []
+    for d in range(1, 8):
+        for n in EDGE_SIZES:
+            t = W.random_table(1, rng, n_lo=n, n_hi=n, families=[fam], dims=[d], seed=d * 7 + n)
+            t[0]["stream_id"] = len(rows)
+            rows.append(t[0])
+    tab = W.empty(len(rows))
+    for i, r in enumerate(rows):
+        tab[i] = r
+    got = zmc.zmc_integrate(zctx.handle, tab)
+    want, _ = oracle.integrate(tab)
+    G.compare(tab, got, want)
+
+
+def test_integrate_every_poly_degree(zctx):
+    rng = np.random.default_rng(5)
+    tab = W.empty(7 * 5 * 3)
+    k = 0
+    for d in range(1, 8):
+        for deg in range(5):
+            for n in (3, 2049, 30001):
+                lo = rng.uniform(-1, 0, size=d)
+                W.poly(tab[k], rng.standard_normal((d, deg + 1)), lo,
+                       lo + rng.uniform(0.5, 2, size=d), n, seed=deg, stream_id=k)
+                k += 1
+    got = zmc.zmc_integrate(zctx.handle, tab)
+    want, _ = oracle.integrate(tab)
+    G.compare(tab, got, want)
+
+
+def test_fig1_batched_matches_oracle_and_closed_form(zctx):
+    import json
+    import os
+
+    tab = W.harmonic_fig1(10**5)
+    got = zmc.zmc_integrate(zctx.handle, tab)
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "fig1_oracle_n1e5.json")))
+    want = np.zeros(100, dtype=[("estimate", "f8"), ("stderr", "f8"), ("mean_abs", "f8")])
+    for key in want.dtype.names:
+        want[key] = [float.fromhex(v) for v in g[key]]
+    G.compare(tab, got, want)
+    for n in range(1, 101):
+        exact = CF.fig1_closed_form(n)
+        assert abs(got["estimate"][n - 1] - exact) <= 5 * got["stderr"][n - 1]
+
+
+def test_fig1_plain_fp64_matches_oracle(zctx):
+    tab = W.harmonic_fig1(10**5)
+    got = zmc.zmc_integrate_plain(zctx.handle, tab)
+    want, _ = oracle.integrate(tab)
+    # FP64 on both sides: only the summation order differs
+    G.compare(tab, got, want, est_rel=1e-11, se_rel=1e-9)
+
+
+def test_plain_fp64_all_families(zctx):
+    tab = W.random_table(60, np.random.default_rng(12), n_lo=1, n_hi=20000)
+    got = zmc.zmc_integrate_plain(zctx.handle, tab)
+    want, _ = oracle.integrate(tab)
+    G.compare(tab, got, want, est_rel=1e-10, se_rel=1e-8)
+
+
+def test_eq2_abslin_batched(zctx):
+    tab = W.abslin_eq2(10**6)
+    got = zmc.zmc_integrate(zctx.handle, tab)
+    want, _ = oracle.integrate(tab)
+    G.compare(tab, got, want)
+    for i, row in enumerate(tab):
+        assert abs(got["estimate"][i] - CF.exact(row)) <= 5 * got["stderr"][i]
+
+
+def test_fig1_ten_repeats_one_launch(zctx):
+    """The paper's 10 independent evaluations (keys 0..9) in one persistent launch:
+    per-n mean over repeats against the closed form, and sampled rows against
+    the oracle."""
+    tab = W.harmonic_fig1(10**6, seeds=range(10))
+    got = zmc.zmc_integrate(zctx.handle, tab)
+    est = got["estimate"].reshape(10, 100)
+    mean = est.mean(axis=0)
+    std = est.std(axis=0, ddof=1)
+    exact = np.array([CF.fig1_closed_form(n) for n in range(1, 101)])
+    assert np.all(np.abs(mean - exact) <= 5 * std / math.sqrt(10) + 1e-12)
+    # the repeat spread against the per-run standard error (chi^2_9 band)
+    ratio = std / got["stderr"].reshape(10, 100).mean(axis=0)
+    assert np.mean((ratio > math.sqrt(1.15 / 9)) & (ratio < math.sqrt(27.9 / 9))) >= 0.98
+    pick = np.arange(0, 1000, 37)
+    want, _ = oracle.integrate(tab[pick])
+    G.compare(tab[pick], got[pick], want)
+
+
+# ------------------------------------------------------------------ invariants
+def test_results_independent_of_batch_composition(zctx):
+    tab = W.random_table(40, np.random.default_rng(21), n_lo=1, n_hi=50000)
+    full = zmc.zmc_integrate(zctx.handle, tab)
+    for sl in (slice(0, 1), slice(5, 17), slice(39, 40), slice(0, 40, 3)):
+        part = zmc.zmc_integrate(zctx.handle, tab[sl])
+        assert np.array_equal(part["estimate"], full["estimate"][sl])
+        assert np.array_equal(part["stderr"], full["stderr"][sl], equal_nan=True)
+
+
+def test_plan_replay_is_bit_identical(zctx):
+    tab = W.mixed(200, gen_seed=3, lo_exp=3, hi_exp=5)
+    plan = zmc.zmc_plan_create(zctx.handle, tab)
+    try:
+        zmc.zmc_plan_run(plan)
+        a = zmc.zmc_plan_results(plan, len(tab))
+        for stages in (zmc.ZMC_STAGE_ALL, zmc.ZMC_STAGE_SAMPLE):
+            zmc.zmc_plan_run(plan, stages)
+            if stages == zmc.ZMC_STAGE_SAMPLE:
+                zmc.zmc_plan_run(plan, zmc.ZMC_STAGE_MERGE)
+            b = zmc.zmc_plan_results(plan, len(tab))
+            assert np.array_equal(a["estimate"], b["estimate"])
+            assert np.array_equal(a["stderr"], b["stderr"], equal_nan=True)
+        one = zmc.zmc_integrate(zctx.handle, tab)
+        assert np.array_equal(a["estimate"], one["estimate"])
+    finally:
+        zmc.zmc_plan_destroy(plan)
+
+
+def test_chunk_length_changes_only_rounding():
+    tab = W.random_table(30, np.random.default_rng(4), n_lo=100, n_hi=40000)
+    want, _ = oracle.integrate(tab)
+    for q in (1, 4, 64):
+        with zmc.Context(arena_bytes=256 << 20, quads_per_lane=q) as c:
+            got = zmc.zmc_integrate(c.handle, tab)
+        G.compare(tab, got, want)
+
+
+def test_special_cases(zctx):
+    t = W.empty(3)
+    W.harmonic(t[0], 1.0, 2.0, [1.0, 2.0], [0.0, 0.0], [1.0, 1.0], 1)
+    W.poly(t[1], [[1.75], [-0.5], [3.0]], [-1.0, 0.0, 0.5], [0.5, 2.0, 1.25], 100000, seed=3)
+    W.gauss(t[2], 1.0, 0.2, [0.0], [0.0], [1.0], 2)
+    got = zmc.zmc_integrate(zctx.handle, t)
+    assert math.isnan(got["stderr"][0])
+    assert got["stderr"][1] == 0.0
+    assert abs(got["estimate"][1] - 1.5 * 2.0 * 0.75 * (1.75 * -0.5 * 3.0)) < 1e-6
+    want, _ = oracle.integrate(t)
+    G.compare(t, got, want)
+
+
+def test_invalid_descriptor_is_rejected(zctx):
+    t = W.harmonic_fig1(10)[:2].copy()
+    t[1]["dim"] = 0
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.zmc_integrate(zctx.handle, t)
+    assert e.value.status == zmc.ZMC_EINVAL
+    # the context is still usable
+    ok = zmc.zmc_integrate(zctx.handle, t[:1])
+    assert ok["status"][0] == 0
+
+
+# ------------------------------------------------------------------ full size
+def test_mixed_1e4_full_size_sampled_rows(zctx):
+    """The 10^4-integrand mix at full size, in the benchmark's plan/graph launch;
+    sampled rows recomputed by the oracle one by one."""
+    tab = W.mixed(10**4)
+    plan = zmc.zmc_plan_create(zctx.handle, tab)
+    try:
+        zmc.zmc_plan_run(plan)
+        got = zmc.zmc_plan_results(plan, len(tab))
+    finally:
+        zmc.zmc_plan_destroy(plan)
+    assert np.array_equal(got["n"], tab["n_samples"])
+    assert np.all(np.isfinite(got["estimate"]))
+    assert np.all(got["stderr"][tab["n_samples"] > 1] >= 0)
+    rng = np.random.default_rng(0)
+    pick = []
+    for fam in range(4):
+        rows = np.nonzero(tab["family"] == fam)[0]
+        pick += list(rng.choice(rows, size=4, replace=False))
+    pick = np.array(sorted(pick))
+    want, _ = oracle.integrate(tab[pick])
+    G.compare(tab[pick], got[pick], want)

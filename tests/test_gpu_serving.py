@@ -1,0 +1,137 @@
+"""Continuous batching through zmc_submit / zmc_poll (GPU)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_10073_gb300 import workloads as W
+from paper_2104_10073_gb300 import zmc
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sctx():
+    from paper_2104_10073_gb300 import build
+
+    build.build()
+    # small iterations so that jobs interleave across many launches
+    c = zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=4096)
+    yield c
+    c.close()
+
+
+def _jobs(n_jobs, seed, max_fns=40, hi_exp=5.5):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        t = W.random_table(int(rng.integers(1, max_fns + 1)), rng, n_lo=1,
+                           n_hi=int(10**hi_exp), seed=j)
+        jobs.append(t)
+    return jobs
+
+
+def test_results_same_alone_and_mixed(sctx, zctx):
+    jobs = _jobs(12, seed=3)
+    # alone: one job at a time through the serving loop
+    alone = []
+    for t in jobs:
+        jid = zmc.zmc_submit(sctx.handle, t)
+        st, res = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=-1)
+        assert st == zmc.ZMC_OK
+        alone.append(res)
+    # mixed: all submitted at once, interleaved over shared persistent launches
+    ids = [zmc.zmc_submit(sctx.handle, t) for t in jobs]
+    for t, jid, a in zip(jobs, ids, alone):
+        st, res = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=-1)
+        assert st == zmc.ZMC_OK
+        assert np.array_equal(res["estimate"], a["estimate"])
+        assert np.array_equal(res["stderr"], a["stderr"], equal_nan=True)
+    # and the same as the blocking batched call and the oracle
+    for t, a in zip(jobs[:4], alone[:4]):
+        one = zmc.zmc_integrate(zctx.handle, t)
+        assert np.array_equal(one["estimate"], a["estimate"])
+        want, _ = oracle.integrate(t)
+        G.compare(t, a, want)
+
+
+def test_poll_semantics(sctx):
+    t = W.mixed(50, gen_seed=9, lo_exp=5.5, hi_exp=6.5)
+    jid = zmc.zmc_submit(sctx.handle, t)
+    st, _ = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=0)
+    assert st in (zmc.ZMC_EAGAIN, zmc.ZMC_OK)
+    if st == zmc.ZMC_OK:
+        pytest.skip("job finished before the first poll")
+    st, res = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=-1)
+    assert st == zmc.ZMC_OK and res is not None
+    st, _ = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=0)
+    assert st == zmc.ZMC_ENOTFOUND
+    st, _ = zmc.zmc_poll(sctx.handle, 987654321, 1, wait_ms=0)
+    assert st == zmc.ZMC_ENOTFOUND
+
+
+def test_timeout_then_complete(sctx):
+    t = W.mixed(200, gen_seed=10, lo_exp=6.5, hi_exp=7.0)
+    jid = zmc.zmc_submit(sctx.handle, t)
+    st, _ = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=1)
+    assert st in (zmc.ZMC_ETIMEOUT, zmc.ZMC_OK)
+    if st != zmc.ZMC_OK:
+        st, _ = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=60000)
+    assert st == zmc.ZMC_OK
+
+
+def test_cancel(sctx):
+    big = W.mixed(300, gen_seed=11, lo_exp=6.5, hi_exp=7.0)
+    jid = zmc.zmc_submit(sctx.handle, big)
+    zmc.zmc_cancel(sctx.handle, jid)
+    st, _ = zmc.zmc_poll(sctx.handle, jid, len(big), wait_ms=-1)
+    assert st in (zmc.ZMC_ECLOSED, zmc.ZMC_OK)
+    # the loop keeps serving after a cancellation
+    small = W.harmonic_fig1(1000)[:5]
+    jid = zmc.zmc_submit(sctx.handle, small)
+    st, res = zmc.zmc_poll(sctx.handle, jid, len(small), wait_ms=-1)
+    assert st == zmc.ZMC_OK
+    want, _ = oracle.integrate(small)
+    G.compare(small, res, want)
+
+
+def test_job_larger_than_budget_is_refused():
+    with zmc.Context(arena_bytes=64 << 20, serving=True) as c:
+        t = W.empty(1)
+        W.harmonic(t[0], 1.0, 1.0, [1.0], [0.0], [1.0], 2**36)  # 2^25 chunks, 256 MiB
+        with pytest.raises(zmc.ZmcError) as e:
+            zmc.zmc_submit(c.handle, t)
+        assert e.value.status == zmc.ZMC_ENOMEM
+
+
+def test_admission_waits_for_memory():
+    """Jobs that do not all fit at once are admitted as earlier ones finish."""
+    with zmc.Context(arena_bytes=96 << 20, serving=True, max_chunks_per_iter=65536) as c:
+        jobs = []
+        for j in range(6):
+            t = W.empty(1)
+            # ~2.4e4 chunks x 8 B records + tables: several jobs exceed the arena together
+            W.harmonic(t[0], 1.0, 0.5, [3.0, 1.0], [0.0, 0.0], [1.0, 1.0], 5 * 10**7, seed=j)
+            jobs.append(t)
+        ids = [zmc.zmc_submit(c.handle, t) for t in jobs]
+        res = [zmc.zmc_poll(c.handle, i, 1, wait_ms=-1) for i in ids]
+        assert all(st == zmc.ZMC_OK for st, _ in res)
+        stats = zmc.zmc_serving_stats_get(c.handle)
+        assert stats["completed"] >= 6
+
+
+def test_poisson_stream_latency_recorded(sctx):
+    jobs = _jobs(30, seed=5, max_fns=20)
+    t0 = time.perf_counter()
+    ids = []
+    for t in jobs:
+        ids.append((zmc.zmc_submit(sctx.handle, t), len(t), time.perf_counter()))
+        time.sleep(0.002)
+    lat = []
+    for jid, n, ts in ids:
+        st, _ = zmc.zmc_poll(sctx.handle, jid, n, wait_ms=-1)
+        assert st == zmc.ZMC_OK
+        lat.append(time.perf_counter() - ts)
+    assert max(lat) < 60.0 and time.perf_counter() - t0 < 120.0
