@@ -26,31 +26,41 @@ __host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t di
 
 // One integrand as the sampling kernel sees it (384 bytes, 16-byte aligned).
 //
+// Every family's amplitude carries a power-of-two scale S (chosen on the host so
+// that S times an upper bound of |f| over the box is ~2^48): the kernel sums the
+// scaled values f' = S f, whose squares stay inside FP32 range for values down
+// to 2^-111 of that bound, and the FP64 merge multiplies by inv_scale = 1/S
+// (exact).
+//
 // Payload words w[] by family (FP32 unless noted; "hi/lo" pairs are an FP64
-// constant split as hi = fl32(c), lo = fl32(c - hi), so that an FMA chain over
-// both halves carries the constant to ~2^-48 relative):
+// constant split as hi = fl32(c), lo = fl32(c - hi), so that FMA chains over
+// both halves carry the constant to ~2^-48 relative).  m_i = word & 0x7FFFFF is
+// the 23-bit sample integer of coordinate i, u_i = m_i 2^-23, v_i = 1 + u_i.
 //   HARMONIC  T_i (u64 two's complement) at w[2i], i < 7: k_i (hi_i-lo_i)/(2 pi) * 2^41,
-//             i.e. turns per unit of the 23-bit sample integer m_i, in units of
-//             2^-64 turn;  P0 (u64) at w[14]: frac(k.lo/(2 pi)) * 2^64;
-//             a w[16], b w[17], -a w[18].
-//   ABSLIN    s = C + sum_i g_i v_i, v_i = 1 + m_i 2^-23 in [1, 2):
-//             g_i = c_i (hi_i - lo_i):  hi w[i], lo w[7+i];
-//             C = sum_i c_i (lo_i - (hi_i - lo_i)):  hi w[14], lo w[15];  a w[16].
-//   GAUSS     t_i = e_i + h_i v_i = (x_i - mu_i) beta, beta^2 = log2(e) / (2 sigma^2):
-//             h_i = (hi_i - lo_i) beta: hi w[i], lo w[7+i];
-//             e_i = (lo_i - (hi_i - lo_i) - mu_i) beta: hi w[14+i], lo w[21+i];
-//             A w[28];  f = A 2^(-sum t_i^2).
-//   POLY      factor i re-expanded in u_i = m_i 2^-23 in [0, 1):
-//             q_i(u) = sum_j e_ij u^j; e_ij hi at w[5i+j], lo at w[35+5i+j].
+//             i.e. turns per unit of m_i, in units of 2^-64 turn;
+//             P0 (u64) at w[14]: frac(k.lo/(2 pi)) * 2^64;  S a w[16], S b w[17], -S a w[18].
+//   ABSLIN    s = C + sum_i g_i v_i:  g_i = c_i (hi_i - lo_i): hi w[i], lo w[7+i];
+//             C = sum_i c_i (lo_i - (hi_i - lo_i)): hi w[14], lo w[15];  S a w[16].
+//   GAUSS     t_i = (x_i - mu_i) beta, beta = sqrt(log2(e) / 2) / sigma, so that
+//             f = A 2^(-sum t_i^2);  h_i = (hi_i - lo_i) beta: hi w[i], lo w[7+i];
+//             S A w[28].  Variant degree 0 ("near": mu_i / box position within
+//             [-1, 2] box widths in every dimension): t_i = h_i (u_i - u0_i) + c0_i
+//             with u0_i the position rounded to a multiple of 2^-23 (w[14+i]), so
+//             u_i - u0_i is exact, and c0_i = -h_i (position - u0_i) (w[21+i]).
+//             Variant degree 1 ("far"): t_i = e_i + h_i u_i, e_i = (lo_i - mu_i) beta:
+//             hi w[14+i], lo w[21+i].
+//   POLY      factor i re-expanded in u_i in [0, 1): q_i(u) = sum_j e_ij u^j;
+//             e_ij hi at w[5i+j], lo at w[35+5i+j] (factor 0 carries S).
 struct alignas(16) FnDev {
   uint32_t variant;
   uint32_t stream_id;
   uint32_t key0, key1;
   uint64_t n_samples;
-  float2 *rec;        // chunk records (mean, M2) of this integrand, one per chunk
+  float2 *rec;        // chunk records (mean', M2') of this integrand, one per chunk
   zmc_result *out;    // result row written by the merge kernel
   double volume;      // prod (hi_i - lo_i), FP64
-  uint32_t pad[4];
+  double inv_scale;   // 1 / S (a power of two)
+  uint32_t pad[2];
   uint32_t w[80];
 };
 static_assert(sizeof(FnDev) == 384, "FnDev layout");

@@ -177,30 +177,61 @@ struct Eval<ZMC_ABSLIN, D, G> {
   }
 };
 
-// A exp(-|x-mu|^2 / (2 sigma^2)) = A 2^(-sum_i t_i^2), t_i = e_i + h_i v_i.
+// A exp(-|x-mu|^2 / (2 sigma^2)) = A 2^(-Z), Z = sum_i t_i^2.  FP32 carries a
+// relative error of ~2^-24 Z in a plainly summed Z, i.e. ~Z 4e-8 in f, which
+// the tails of narrow Gaussians (Z of tens) cannot afford.  So t_i is formed as
+// an unevaluated pair th + tl (exact product th = fl(h_hi d), its rounding error,
+// and the small terms), t_i^2 as qh + c with qh = th^2 and c = (qh's error) +
+// 2 th tl, Z as zh + zl with every addition's rounding error kept (TwoSum), and
+// f = A 2^-zh (1 - ln2 zl).  Degree 0 / 1 select how t_i is formed (see FnDev).
 template <int D, int G>
 struct Eval<ZMC_GAUSS, D, G> {
-  float hh[D], hl[D], eh[D], el[D];
+  float hh[D], hl[D], pa[D], pb[D];
   float A;
   __device__ __forceinline__ void load(const FnDev *fn) {
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       hh[i] = __uint_as_float(fn->w[i]);
       hl[i] = __uint_as_float(fn->w[7 + i]);
-      eh[i] = __uint_as_float(fn->w[14 + i]);
-      el[i] = __uint_as_float(fn->w[21 + i]);
+      pa[i] = __uint_as_float(fn->w[14 + i]);
+      pb[i] = __uint_as_float(fn->w[21 + i]);
     }
     A = __uint_as_float(fn->w[28]);
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
-    float z = 0.0f;
+    float zh = 0.0f, zl = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      const float v = unit_v(r[i]);
-      const float t = fmaf(hh[i], v, eh[i]) + fmaf(hl[i], v, el[i]);
-      z = fmaf(t, t, z);
+      const float u = unit_v(r[i]) - 1.0f;  // exact
+      float th, tl;
+      if (G == 0) {
+        const float d = u - pa[i];  // exact: both are multiples of 2^-23, |d| < 2
+        th = hh[i] * d;
+        tl = fmaf(hh[i], d, -th) + fmaf(hl[i], d, pb[i]);
+      } else {
+        const float ph = hh[i] * u;
+        const float pl = fmaf(hh[i], u, -ph);
+        const float s = pa[i] + ph;  // TwoSum(e_hi, h_hi u)
+        const float bb = s - pa[i];
+        const float err = (pa[i] - (s - bb)) + (ph - bb);
+        th = s;
+        tl = err + pl + fmaf(hl[i], u, pb[i]);
+      }
+      const float qh = th * th;
+      const float c = fmaf(th + th, tl, fmaf(th, th, -qh));
+      if (i == 0) {
+        zh = qh;
+        zl = c;
+      } else {
+        const float s = zh + qh;  // TwoSum(zh, qh)
+        const float bb = s - zh;
+        const float err = (zh - (s - bb)) + (qh - bb);
+        zh = s;
+        zl += err + c;
+      }
     }
-    return A * ex2_approx(-z);
+    const float e = A * ex2_approx(-zh);
+    return fmaf(e, -0.69314718055994531f * zl, e);
   }
 };
 
@@ -333,9 +364,10 @@ __device__ __forceinline__ void run_item(const FnDev *__restrict__ fn, uint64_t 
   ZMC_VARIANTS_DIM(X, ZMC_POLY, 0) ZMC_VARIANTS_DIM(X, ZMC_POLY, 1)                  \
   ZMC_VARIANTS_DIM(X, ZMC_POLY, 2) ZMC_VARIANTS_DIM(X, ZMC_POLY, 3)                  \
   ZMC_VARIANTS_DIM(X, ZMC_POLY, 4)
+#define ZMC_GAUSS_VARIANTS(X) ZMC_VARIANTS_DIM(X, ZMC_GAUSS, 0) ZMC_VARIANTS_DIM(X, ZMC_GAUSS, 1)
 #define ZMC_ALL_VARIANTS(X)                                                          \
   ZMC_VARIANTS_DIM(X, ZMC_HARMONIC, 0) ZMC_VARIANTS_DIM(X, ZMC_ABSLIN, 0)            \
-  ZMC_VARIANTS_DIM(X, ZMC_GAUSS, 0) ZMC_POLY_VARIANTS(X)
+  ZMC_GAUSS_VARIANTS(X) ZMC_POLY_VARIANTS(X)
 
 __device__ __forceinline__ uint32_t find_entry(const Entry *__restrict__ entries, uint32_t ne,
                                                uint64_t item, uint32_t hint) {
@@ -369,7 +401,7 @@ __device__ __forceinline__ void dispatch_family(const FnDev *fn, uint64_t chunk,
       } else if (FAM == ZMC_ABSLIN) {
         switch (fn->variant) { ZMC_FAM_CASES(ZMC_ABSLIN) default: break; }
       } else if (FAM == ZMC_GAUSS) {
-        switch (fn->variant) { ZMC_FAM_CASES(ZMC_GAUSS) default: break; }
+        switch (fn->variant) { ZMC_GAUSS_VARIANTS(ZMC_CASE) default: break; }
       } else {
         switch (fn->variant) { ZMC_POLY_VARIANTS(ZMC_CASE) default: break; }
       }
@@ -443,11 +475,12 @@ __global__ void __launch_bounds__(256) zmc_merge_kernel(const FnDev *const *__re
       const double dm = static_cast<double>(rc.x) - mean;
       m += fma(nc * dm, dm, static_cast<double>(rc.y));
     }
-    const double m2 = fmax(warp_sum_f64(m), 0.0);
+    const double inv = fn->inv_scale;
+    const double m2 = fmax(warp_sum_f64(m), 0.0) * inv * inv;
     if (lane == 0) {
       const double nd = static_cast<double>(N);
       zmc_result res;
-      res.estimate = fn->volume * mean;
+      res.estimate = fn->volume * (mean * inv);
       res.stderr_ = fn->volume * sqrt(m2 / (nd * (nd - 1.0)));
       res.n = N;
       res.status = ZMC_OK;
@@ -612,7 +645,8 @@ __device__ __forceinline__ void eval_range(const FnDev *fn, uint64_t s_begin, ui
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const uint64_t s = 4 * q + t;
-      if (s >= s_begin && s < s_begin + count) out[s - s_begin] = ev(r + t * D);
+      if (s >= s_begin && s < s_begin + count)
+        out[s - s_begin] = static_cast<float>(static_cast<double>(ev(r + t * D)) * fn->inv_scale);
     }
   }
 }

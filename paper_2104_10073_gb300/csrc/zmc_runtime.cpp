@@ -144,13 +144,58 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
     if (!std::isfinite(d.p[j])) return set_error(ZMC_EINVAL, "parameter p[%d] not finite", j);
 
   std::memset(fn, 0, sizeof(FnDev));
+  const double *p = d.p;
+  // An upper bound of |f| over the box; the kernel works on S f with
+  // S = 2^(48 - ceil(log2 bound)) (clamped), undone exactly in the merge.
+  double fsup = 0.0;
+  double poly_e[kMaxDim][5] = {{0}};
+  switch (d.family) {
+    case ZMC_HARMONIC:
+      fsup = std::fabs(p[0]) + std::fabs(p[1]);
+      break;
+    case ZMC_ABSLIN: {
+      double up = 0.0, dn = 0.0;
+      for (int i = 0; i < dim; ++i) {
+        const double c = p[1 + i];
+        up += c * (c > 0 ? d.hi[i] : d.lo[i]);
+        dn += c * (c > 0 ? d.lo[i] : d.hi[i]);
+      }
+      fsup = std::fabs(p[0]) * std::max(std::fabs(up), std::fabs(dn));
+      break;
+    }
+    case ZMC_GAUSS:
+      fsup = std::fabs(p[0]);
+      break;
+    default: {  // POLY: q_i(u) = sum_j c_ij (lo_i + w_i u)^j = sum_k e_ik u^k
+      const int g = static_cast<int>(d.deg);
+      fsup = 1.0;
+      for (int i = 0; i < dim; ++i) {
+        double bound = 0.0;
+        for (int k = 0; k <= g; ++k) {
+          double e = 0.0;
+          for (int j = k; j <= g; ++j)
+            e += p[5 * i + j] * binom(j, k) * std::pow(d.lo[i], j - k) * std::pow(w[i], k);
+          poly_e[i][k] = e;
+          bound += std::fabs(e);
+        }
+        fsup *= bound;
+      }
+      break;
+    }
+  }
+  int sexp = 0;
+  if (fsup > 0.0 && std::isfinite(fsup)) {
+    sexp = 48 - static_cast<int>(std::ceil(std::log2(fsup)));
+    sexp = std::max(-100, std::min(100, sexp));
+  }
+  const double S = std::ldexp(1.0, sexp);
   fn->variant = variant_code(d.family, d.dim, d.family == ZMC_POLY ? d.deg : 0);
   fn->stream_id = d.stream_id;
   fn->key0 = static_cast<uint32_t>(d.seed);
   fn->key1 = static_cast<uint32_t>(d.seed >> 32);
   fn->n_samples = d.n_samples;
   fn->volume = vol;
-  const double *p = d.p;
+  fn->inv_scale = std::ldexp(1.0, -sexp);
   bool ok = true;
   switch (d.family) {
     case ZMC_HARMONIC: {
@@ -168,10 +213,10 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
       if (!(std::fabs(phi) < 4.0e15)) return set_error(ZMC_EINVAL, "harmonic phase too large");
       const double fr = phi - std::floor(phi);  // exact, in [0, 1)
       w64[7] = static_cast<uint64_t>(std::ldexp(fr, 64));
-      ok = finite_f32(p[0]) && finite_f32(p[1]);
-      put_f32(&fn->w[16], p[0]);
-      put_f32(&fn->w[17], p[1]);
-      put_f32(&fn->w[18], -p[0]);
+      ok = finite_f32(S * p[0]) && finite_f32(S * p[1]);
+      put_f32(&fn->w[16], S * p[0]);
+      put_f32(&fn->w[17], S * p[1]);
+      put_f32(&fn->w[18], -S * p[0]);
       break;
     }
     case ZMC_ABSLIN: {
@@ -182,33 +227,45 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
         split(g, &fn->w[i], &fn->w[7 + i]);
         C += p[1 + i] * (d.lo[i] - w[i]);
       }
-      ok = ok && finite_f32(C) && finite_f32(p[0]);
+      ok = ok && finite_f32(C) && finite_f32(S * p[0]);
       split(C, &fn->w[14], &fn->w[15]);
-      put_f32(&fn->w[16], p[0]);
+      put_f32(&fn->w[16], S * p[0]);
       break;
     }
     case ZMC_GAUSS: {
       const double sigma = p[1];
       if (!(sigma > 0.0)) return set_error(ZMC_EINVAL, "gauss sigma must be > 0");
       const double beta = std::sqrt(1.4426950408889634073599246810019 / 2.0) / sigma;
+      bool near = true;
+      double pos[kMaxDim];
+      for (int i = 0; i < dim; ++i) {
+        pos[i] = (p[2 + i] - d.lo[i]) / w[i];  // mu_i in units of the box width from lo_i
+        if (!(pos[i] >= -1.0 && pos[i] <= 2.0)) near = false;
+      }
       for (int i = 0; i < dim; ++i) {
         const double h = w[i] * beta;
-        const double e = (d.lo[i] - w[i] - p[2 + i]) * beta;
-        ok = ok && finite_f32(h) && finite_f32(e);
+        ok = ok && finite_f32(h);
         split(h, &fn->w[i], &fn->w[7 + i]);
-        split(e, &fn->w[14 + i], &fn->w[21 + i]);
+        if (near) {
+          const double u0 = std::ldexp(std::nearbyint(std::ldexp(pos[i], 23)), -23);
+          put_f32(&fn->w[14 + i], u0);                       // exact
+          put_f32(&fn->w[21 + i], -h * (pos[i] - u0));        // |.| <= h 2^-24
+        } else {
+          const double e = (d.lo[i] - p[2 + i]) * beta;
+          ok = ok && finite_f32(e);
+          split(e, &fn->w[14 + i], &fn->w[21 + i]);
+        }
       }
-      ok = ok && finite_f32(p[0]);
-      put_f32(&fn->w[28], p[0]);
+      fn->variant = variant_code(ZMC_GAUSS, d.dim, near ? 0 : 1);
+      ok = ok && finite_f32(S * p[0]);
+      put_f32(&fn->w[28], S * p[0]);
       break;
     }
-    default: {  // POLY: q_i(u) = sum_j c_ij (lo_i + w_i u)^j = sum_k e_ik u^k
+    default: {
       const int g = static_cast<int>(d.deg);
       for (int i = 0; i < dim; ++i) {
         for (int k = 0; k <= g; ++k) {
-          double e = 0.0;
-          for (int j = k; j <= g; ++j)
-            e += p[5 * i + j] * binom(j, k) * std::pow(d.lo[i], j - k) * std::pow(w[i], k);
+          const double e = (i == 0 ? S : 1.0) * poly_e[i][k];
           ok = ok && finite_f32(e);
           split(e, &fn->w[5 * i + k], &fn->w[35 + 5 * i + k]);
         }
