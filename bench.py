@@ -258,27 +258,31 @@ def run_native(args, world, rank, local):
     assert np.all(res["status"] == 0)
 
     # plain FP64 form, same table, one launch per integrand
-    plain_steps = max(1, min(args.steps, 3))
-    zmc.zmc_plan_run_plain(plan)
-    ctx.stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(ctx.stream)
-    for _ in range(plain_steps):
+    plain_ms = None
+    if not args.skip_plain:
+        plain_steps = max(1, min(args.steps, 3))
         zmc.zmc_plan_run_plain(plan)
-    e1.record(ctx.stream)
-    ctx.stream.synchronize()
-    plain_ms = e0.elapsed_time(e1) / plain_steps
+        ctx.stream.synchronize()
+        e0.record(ctx.stream)
+        for _ in range(plain_steps):
+            zmc.zmc_plan_run_plain(plan)
+        e1.record(ctx.stream)
+        ctx.stream.synchronize()
+        plain_ms = e0.elapsed_time(e1) / plain_steps
     zmc.zmc_plan_destroy(plan)
 
     # end to end through the public blocking call: host table in, host results out
-    e2e_t = []
-    for k in range(args.steps + 1):
-        t0 = time.perf_counter()
-        out = zmc.zmc_integrate(ctx.handle, tab)
-        if k > 0:
-            e2e_t.append(time.perf_counter() - t0)
-    assert np.all(out["status"] == 0)
-    e2e_s = max_over_ranks(world, sum(e2e_t) / len(e2e_t))
+    e2e_s = None
+    if not args.skip_e2e:
+        e2e_t = []
+        for k in range(args.steps + 1):
+            t0 = time.perf_counter()
+            out = zmc.zmc_integrate(ctx.handle, tab)
+            if k > 0:
+                e2e_t.append(time.perf_counter() - t0)
+        assert np.all(out["status"] == 0)
+        e2e_s = max_over_ranks(world, sum(e2e_t) / len(e2e_t))
 
     # the 10^4-integrand mix (batched and plain), rank 0 only
     mixed = None
@@ -325,16 +329,17 @@ def run_native(args, world, rank, local):
                    "quads_per_lane": info["quads_per_lane"], "chunks": info["n_chunks"],
                    "grid": info["grid"], "block": info["block"],
                    "l2": "flushed between steps (256 MiB write, outside the timed events)"},
-        "plain": {"value": n_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT,
-                  "ms_per_step": plain_ms, "dtype": "f64",
-                  "form": "one FP64 kernel launch per integrand + merge"},
-        "batched_over_plain": plain_ms / (sum(step_ms) / len(step_ms)),
+        "plain": None if plain_ms is None else {
+            "value": n_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": plain_ms,
+            "dtype": "f64", "form": "one FP64 kernel launch per integrand + merge"},
+        "batched_over_plain": None if plain_ms is None else plain_ms / (sum(step_ms) / len(step_ms)),
         "mixed": mixed,
         "serving": serving,
-        "e2e": {"value": total / e2e_s / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": len(tab) * W.DESC_DTYPE.itemsize,
-                "d2h_bytes_per_step": len(tab) * 32,
-                "path": "zmc_integrate (host table in, host results out)"},
+        "e2e": None if e2e_s is None else {
+            "value": total / e2e_s / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": len(tab) * W.DESC_DTYPE.itemsize,
+            "d2h_bytes_per_step": len(tab) * 32,
+            "path": "zmc_integrate (host table in, host results out)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": None,
                      "kernel": "zmc_batched_kernel<HARMONIC>",
@@ -405,6 +410,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-mixed", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=100.0)
     ap.add_argument("--serving-seconds", type=float, default=10.0)
     args = ap.parse_args()

@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp"]
-HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_sincos_coeffs.h"]
+HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h"]
 
 
 def _nvcc() -> str:
@@ -32,8 +32,11 @@ def _nvcc() -> str:
 
 
 def _flags(extra=()):
+    # ZMC_NVCC_DEFINES: optional space-separated -D tuning knobs (launch bounds,
+    # multiply form) for sweeps; the defaults are the tuned values.
+    defs = os.environ.get("ZMC_NVCC_DEFINES", "").split()
     return [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-            "-I", CSRC, *extra]
+            "-I", CSRC, *defs, *extra]
 
 
 def _newest_input() -> float:

@@ -1,18 +1,20 @@
-"""Fit the FP32 polynomials for sin(2 pi t) and cos(2 pi t) on |t| <= 1/8 turn.
+"""Fit the FP32 polynomials the kernels evaluate instead of library calls.
 
-The kernels reduce every phase to a quarter-turn index q and a remainder t in
-[-1/8, 1/8] turns (exactly, in fixed point), then evaluate
+* sin(2 pi t), cos(2 pi t) on |t| <= 1/8 turn.  The kernels reduce every phase
+  to a quarter-turn index q and a remainder t in [-1/8, 1/8] turns (exactly, in
+  fixed point), then evaluate
+      sin(2 pi t) ~= t * (S0 + S1 t^2 + S2 t^4 + S3 t^6)
+      cos(2 pi t) ~= C0 + C1 t^2 + C2 t^4 + C3 t^6 + C4 t^8
+  fitted in the variable z = t^2 (absolute error for cos; the error of
+  sin(2 pi t)/t weighted by |t| for sin).
+* 2^x on |x| <= 0.51 (relative error), degree 6: the Gaussian family's
+  2^-Z = 2^-n 2^-r after n = rint(Z).
 
-    sin(2 pi t) ~= t * (S0 + S1 t^2 + S2 t^4 + S3 t^6)
-    cos(2 pi t) ~= C0 + C1 t^2 + C2 t^4 + C3 t^6 + C4 t^8
+Every fit is a Remez exchange carried out in 50-digit arithmetic, then rounded to
+binary32.  The script prints the maximum error of the rounded polynomials
+evaluated in FP64 on a dense grid and writes ``zmc_coeffs.h``.
 
-The coefficients are found here by a Remez exchange on the weighted error in
-the variable z = t^2 (absolute error for cos; error of sin(2 pi t)/t weighted by
-|t| for sin), carried out in 50-digit arithmetic, then rounded to binary32.
-The script prints the maximum error of the rounded polynomials evaluated in
-FP64 on a dense grid and writes ``zmc_sincos_coeffs.h``.
-
-Run from the repository root:  python paper_2104_10073_gb300/csrc/gen_sincos.py
+Run from the repository root:  python paper_2104_10073_gb300/csrc/gen_coeffs.py
 """
 import os
 
@@ -24,11 +26,11 @@ T_MAX = mpmath.mpf(1) / 8
 Z_MAX = T_MAX**2
 
 
-def remez(target, weight, n_coef, iters=30):
-    """Minimax polynomial p(z) = sum c_j z^j of weight(z) * (target(z) - p(z)) on [0, Z_MAX]."""
+def remez(target, weight, n_coef, iters=30, a=mpmath.mpf(0), b=Z_MAX):
+    """Minimax polynomial p(z) = sum c_j z^j of weight(z) * (target(z) - p(z)) on [a, b]."""
     m = n_coef + 1
     # Chebyshev extrema as the first reference
-    ref = [Z_MAX * (1 - mpmath.cos(mpmath.pi * i / (m - 1))) / 2 for i in range(m)]
+    ref = [a + (b - a) * (1 - mpmath.cos(mpmath.pi * i / (m - 1))) / 2 for i in range(m)]
     coef = None
     for _ in range(iters):
         A = mpmath.matrix(m, m)
@@ -45,7 +47,7 @@ def remez(target, weight, n_coef, iters=30):
             return weight(z) * (target(z) - sum(c * z**j for j, c in enumerate(coef)))
 
         # new reference: extrema of the error on a fine grid, one per sign run
-        grid = [Z_MAX * (1 - mpmath.cos(mpmath.pi * i / 4000)) / 2 for i in range(4001)]
+        grid = [a + (b - a) * (1 - mpmath.cos(mpmath.pi * i / 4000)) / 2 for i in range(4001)]
         vals = [err(z) for z in grid]
         runs = []
         start = 0
@@ -84,19 +86,29 @@ def main():
     pc = sum(float(v) * z**j for j, v in enumerate(c32))
     es = np.max(np.abs(ps - np.sin(2 * np.pi * t)))
     ec = np.max(np.abs(pc - np.cos(2 * np.pi * t)))
-    print(f"max |sin err| {es:.3e}  max |cos err| {ec:.3e}")
+    xm = mpmath.mpf("0.51")
+    e2 = remez(lambda x: mpmath.power(2, x), lambda x: 1 / mpmath.power(2, x), 7, a=-xm, b=xm)
+    e32 = [np.float32(float(v)) for v in e2]
+    x = np.linspace(-0.51, 0.51, 200001)
+    pe = sum(float(v) * x**j for j, v in enumerate(e32))
+    ee = np.max(np.abs(pe / np.exp2(x) - 1))
+    print(f"max |sin err| {es:.3e}  max |cos err| {ec:.3e}  max |exp2 rel err| {ee:.3e}")
     here = os.path.dirname(os.path.abspath(__file__))
     lines = [
-        "// Generated by gen_sincos.py: Remez fits of sin(2 pi t)/t and cos(2 pi t) in",
-        "// z = t^2 on |t| <= 1/8 turn, rounded to binary32.  Max error of the rounded",
-        f"// polynomials in exact arithmetic: sin {es:.2e}, cos {ec:.2e}.",
+        "// Generated by gen_coeffs.py: Remez fits rounded to binary32.  Max error of the",
+        "// rounded polynomials in exact arithmetic:",
+        f"//   sin(2 pi t), |t| <= 1/8 (in t^2): {es:.2e} absolute",
+        f"//   cos(2 pi t), |t| <= 1/8 (in t^2): {ec:.2e} absolute",
+        f"//   2^x, |x| <= 0.51, degree 6:       {ee:.2e} relative",
         "#pragma once",
     ]
     for j, v in enumerate(s32):
         lines.append(f"#define ZMC_SIN_C{j} {float(v).hex()}f  // {float(v):.9e}")
     for j, v in enumerate(c32):
         lines.append(f"#define ZMC_COS_C{j} {float(v).hex()}f  // {float(v):.9e}")
-    with open(os.path.join(here, "zmc_sincos_coeffs.h"), "w") as f:
+    for j, v in enumerate(e32):
+        lines.append(f"#define ZMC_EXP2_C{j} {float(v).hex()}f  // {float(v):.9e}")
+    with open(os.path.join(here, "zmc_coeffs.h"), "w") as f:
         f.write("\n".join(lines) + "\n")
 
 

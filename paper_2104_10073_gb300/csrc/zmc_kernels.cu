@@ -23,7 +23,7 @@
 #include <cstdint>
 
 #include "zmc_internal.h"
-#include "zmc_sincos_coeffs.h"
+#include "zmc_coeffs.h"
 
 namespace zmc {
 namespace {
@@ -52,16 +52,28 @@ __device__ __forceinline__ RoundKeys make_round_keys(uint32_t key0, uint32_t key
 }
 
 // Ten rounds of the 4x32 S-box: two 32x32->64 products, two three-way XORs.
+// ZMC_PHILOX_MULHI selects separate high / low multiplies instead of one
+// widening multiply per product (same results; a scheduling choice).
+#ifndef ZMC_PHILOX_MULHI
+#define ZMC_PHILOX_MULHI 0
+#endif
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                         const RoundKeys &rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
+#if ZMC_PHILOX_MULHI
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+#else
     const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
     const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
-    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ rk.k0[r];
-    const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ rk.k1[r];
-    c1 = static_cast<uint32_t>(p1);
-    c3 = static_cast<uint32_t>(p0);
+    const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+    const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+#endif
+    const uint32_t n0 = hi1 ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = hi0 ^ c3 ^ rk.k1[r];
+    c1 = lo1;
+    c3 = lo0;
     c0 = n0;
     c2 = n2;
   }
@@ -99,10 +111,24 @@ __device__ __forceinline__ float unit_v(uint32_t word) {
   return __uint_as_float((word & 0x7FFFFFu) | 0x3F800000u);
 }
 
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
+// 2^-(zh + zl) for zh >= 0, |zl| << 1, times amp: n = rint(zh) by the 1.5*2^23
+// rounding constant (exact for the clamped zh), r = zh - n exact, 2^-(r + zl) by the
+// degree-6 fit of 2^x on |x| <= 0.51, and 2^-n as an exponent field (0 when
+// n > 126, i.e. below the normal range).  All on the FMA and ALU pipes.
+__device__ __forceinline__ float amp_exp2_neg(float amp, float zh, float zl) {
+  zh = fminf(zh, 200.0f);  // 2^-200 is already 0 here; keeps x inside the fit
+  const float big = zh + 12582912.0f;
+  const float n = big - 12582912.0f;
+  const float x = (n - zh) - zl;  // -(r + zl)
+  float p = fmaf(ZMC_EXP2_C6, x, ZMC_EXP2_C5);
+  p = fmaf(p, x, ZMC_EXP2_C4);
+  p = fmaf(p, x, ZMC_EXP2_C3);
+  p = fmaf(p, x, ZMC_EXP2_C2);
+  p = fmaf(p, x, ZMC_EXP2_C1);
+  p = fmaf(p, x, ZMC_EXP2_C0);
+  const int ni = __float_as_int(big) - 0x4B400000;  // n as an integer
+  const int eb = max(127 - ni, 0);                  // biased exponent of 2^-n, or 0
+  return (amp * p) * __int_as_float(eb << 23);
 }
 
 // ---------------------------------------------------------------- integrands (FP32)
@@ -183,7 +209,7 @@ struct Eval<ZMC_ABSLIN, D, G> {
 // an unevaluated pair th + tl (exact product th = fl(h_hi d), its rounding error,
 // and the small terms), t_i^2 as qh + c with qh = th^2 and c = (qh's error) +
 // 2 th tl, Z as zh + zl with every addition's rounding error kept (TwoSum), and
-// f = A 2^-zh (1 - ln2 zl).  Degree 0 / 1 select how t_i is formed (see FnDev).
+// f = A 2^-(zh + zl).  Degree 0 / 1 select how t_i is formed (see FnDev).
 template <int D, int G>
 struct Eval<ZMC_GAUSS, D, G> {
   float hh[D], hl[D], pa[D], pb[D];
@@ -230,8 +256,7 @@ struct Eval<ZMC_GAUSS, D, G> {
         zl += err + c;
       }
     }
-    const float e = A * ex2_approx(-zh);
-    return fmaf(e, -0.69314718055994531f * zl, e);
+    return amp_exp2_neg(A, zh, zl);
   }
 };
 
@@ -416,8 +441,31 @@ __device__ __forceinline__ void dispatch_family(const FnDev *fn, uint64_t chunk,
 // counter until the family's items run out; an item is one chunk of one
 // integrand.  Items are grouped by variant so co-resident warps mostly run the
 // same code.
+// Resident 256-thread blocks per SM each family kernel is compiled for (it caps
+// registers at 65536 / (256 * n)); overridable per family at build time.
+#ifndef ZMC_MIN_BLOCKS_HARMONIC
+#define ZMC_MIN_BLOCKS_HARMONIC 2
+#endif
+#ifndef ZMC_MIN_BLOCKS_ABSLIN
+#define ZMC_MIN_BLOCKS_ABSLIN 2
+#endif
+#ifndef ZMC_MIN_BLOCKS_GAUSS
+#define ZMC_MIN_BLOCKS_GAUSS 2
+#endif
+#ifndef ZMC_MIN_BLOCKS_POLY
+#define ZMC_MIN_BLOCKS_POLY 2
+#endif
 template <int FAM>
-__global__ void __launch_bounds__(256, 2) zmc_batched_kernel(const Entry *__restrict__ entries,
+struct MinBlocks {
+  static constexpr int value = FAM == ZMC_HARMONIC ? ZMC_MIN_BLOCKS_HARMONIC
+                               : FAM == ZMC_ABSLIN ? ZMC_MIN_BLOCKS_ABSLIN
+                               : FAM == ZMC_GAUSS  ? ZMC_MIN_BLOCKS_GAUSS
+                                                   : ZMC_MIN_BLOCKS_POLY;
+};
+
+template <int FAM>
+__global__ void __launch_bounds__(256, MinBlocks<FAM>::value)
+    zmc_batched_kernel(const Entry *__restrict__ entries,
                                                           LaunchHdr *__restrict__ hdr) {
   const uint32_t lane = threadIdx.x & 31u;
   const unsigned long long begin = hdr->item_begin[FAM];
