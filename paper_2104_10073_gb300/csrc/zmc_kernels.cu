@@ -117,9 +117,9 @@ __device__ __forceinline__ float unit_v(uint32_t word) {
 // n > 126, i.e. below the normal range).  All on the FMA and ALU pipes.
 __device__ __forceinline__ float amp_exp2_neg(float amp, float zh, float zl) {
   zh = fminf(zh, 200.0f);  // 2^-200 is already 0 here; keeps x inside the fit
-  const float big = zh + 12582912.0f;
-  const float n = big - 12582912.0f;
-  const float x = (n - zh) - zl;  // -(r + zl)
+  const float big = __fadd_rn(zh, 12582912.0f);
+  const float n = __fsub_rn(big, 12582912.0f);
+  const float x = __fsub_rn(__fsub_rn(n, zh), zl);  // -(r + zl)
   float p = fmaf(ZMC_EXP2_C6, x, ZMC_EXP2_C5);
   p = fmaf(p, x, ZMC_EXP2_C4);
   p = fmaf(p, x, ZMC_EXP2_C3);
@@ -161,7 +161,7 @@ struct Eval<ZMC_HARMONIC, D, G> {
     const uint32_t g = static_cast<uint32_t>(acc >> 32) + 0x20000000u;  // + 1/8 turn
     const uint32_t q = g >> 30;                                          // nearest quarter
     // bits 7..29 of g: the remainder (+1/8) truncated to 2^-25 turn, as 2^23 + Y
-    const float yf = __uint_as_float(((g >> 7) & 0x7FFFFFu) | 0x4B000000u) - 12582912.0f;
+    const float yf = __fsub_rn(__uint_as_float(((g >> 7) & 0x7FFFFFu) | 0x4B000000u), 12582912.0f);
     const float t = fmaf(yf, 0x1p-25f, 0x1p-26f);  // midpoint of the truncated bits
     const float z = t * t;
     const float s =
@@ -224,36 +224,39 @@ struct Eval<ZMC_GAUSS, D, G> {
     }
     A = __uint_as_float(fn->w[28]);
   }
+  // The products and sums of the error-free transformations use the _rn
+  // intrinsics: the compiler never contracts those into an FMA, which would
+  // change the rounded value the error terms are computed against.
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
     float zh = 0.0f, zl = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      const float u = unit_v(r[i]) - 1.0f;  // exact
+      const float u = __fsub_rn(unit_v(r[i]), 1.0f);  // exact
       float th, tl;
       if (G == 0) {
-        const float d = u - pa[i];  // exact: both are multiples of 2^-23, |d| < 2
-        th = hh[i] * d;
-        tl = fmaf(hh[i], d, -th) + fmaf(hl[i], d, pb[i]);
+        const float d = __fsub_rn(u, pa[i]);  // exact: multiples of 2^-23, |d| < 2
+        th = __fmul_rn(hh[i], d);
+        tl = __fadd_rn(fmaf(hh[i], d, -th), fmaf(hl[i], d, pb[i]));
       } else {
-        const float ph = hh[i] * u;
+        const float ph = __fmul_rn(hh[i], u);
         const float pl = fmaf(hh[i], u, -ph);
-        const float s = pa[i] + ph;  // TwoSum(e_hi, h_hi u)
-        const float bb = s - pa[i];
-        const float err = (pa[i] - (s - bb)) + (ph - bb);
+        const float s = __fadd_rn(pa[i], ph);  // TwoSum(e_hi, h_hi u)
+        const float bb = __fsub_rn(s, pa[i]);
+        const float err = __fadd_rn(__fsub_rn(pa[i], __fsub_rn(s, bb)), __fsub_rn(ph, bb));
         th = s;
-        tl = err + pl + fmaf(hl[i], u, pb[i]);
+        tl = __fadd_rn(__fadd_rn(err, pl), fmaf(hl[i], u, pb[i]));
       }
-      const float qh = th * th;
-      const float c = fmaf(th + th, tl, fmaf(th, th, -qh));
+      const float qh = __fmul_rn(th, th);
+      const float c = fmaf(__fadd_rn(th, th), tl, fmaf(th, th, -qh));
       if (i == 0) {
         zh = qh;
         zl = c;
       } else {
-        const float s = zh + qh;  // TwoSum(zh, qh)
-        const float bb = s - zh;
-        const float err = (zh - (s - bb)) + (qh - bb);
+        const float s = __fadd_rn(zh, qh);  // TwoSum(zh, qh)
+        const float bb = __fsub_rn(s, zh);
+        const float err = __fadd_rn(__fsub_rn(zh, __fsub_rn(s, bb)), __fsub_rn(qh, bb));
         zh = s;
-        zl += err + c;
+        zl = __fadd_rn(zl, __fadd_rn(err, c));
       }
     }
     return amp_exp2_neg(A, zh, zl);
@@ -318,9 +321,22 @@ __device__ __forceinline__ void warp_chan_merge(float &n, float &mean, float &m2
 }
 
 // Samples [chunk * 128Q, min(+128Q, N)) of one integrand.  Lane l takes quads
-// l, l+32, ..., l+32(Q-1) of the chunk, accumulates sum (f - K) and
-// sum (f - K)^2 in FP32 with K = its first sample's value, converts to
-// (n, mean, M2), and the warp merges the 32 summaries.
+// l, l+32, ..., l+32(Q-1) of the chunk.  Over each block of kBlockQuads of its
+// quads it accumulates in FP32
+//   s1 = sum f            (each quad summed pairwise first; unshifted, so its
+//                          rounding error scales with the values themselves)
+//   s2 = sum (f - K)^2    (K = the block's first value, so that s2 does not hold
+//                          mean^2 n when the spread is small)
+// turns them into (n, mean = s1/n, M2 = s2 - n (mean - K)^2) and merges that into
+// the lane's running summary (Chan's pairwise update); the warp then merges the
+// 32 lane summaries the same way.
+#ifndef ZMC_QUAD_UNROLL
+#define ZMC_QUAD_UNROLL 1
+#endif
+constexpr int kQuadUnroll = ZMC_QUAD_UNROLL;  // quads of one lane interleaved per step
+// Quads per accumulation block: a lane's shifted sums never span more than
+// 4 * kBlockQuads samples, which bounds their rounding error for any chunk length.
+constexpr uint32_t kBlockQuads = 16;
 template <int FAM, int D, int G, bool FAST>
 __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t chunk,
                                           uint32_t Q, uint32_t lane) {
@@ -337,33 +353,55 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
   const uint32_t base_lo0 = static_cast<uint32_t>(block0) + lane * D;
   const uint32_t base_hi = static_cast<uint32_t>(block0 >> 32);
 
-  float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
-  uint32_t cnt = 0;
-  for (uint32_t j = 0; j < Q; ++j) {
-    const uint32_t ql = lane + 32u * j;
-    if (!FAST && 4u * ql >= nc) break;
-    uint32_t r[4 * D];
-    gen_quad<D, FAST>(quad0 + ql, base_lo0 + 32u * D * j, base_hi, sid, rk, r);
-    float f[4];
+  // running (n, mean, M2) of the lane, merged from blocks of kBlockQuads quads
+  float n = 0.0f, mean = 0.0f, m2 = 0.0f;
+  for (uint32_t jb = 0; jb < Q; jb += kBlockQuads) {
+    const uint32_t je = jb + kBlockQuads < Q ? jb + kBlockQuads : Q;
+    float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    uint32_t cnt = 0;
+#pragma unroll kQuadUnroll
+    for (uint32_t j = jb; j < je; ++j) {
+      const uint32_t ql = lane + 32u * j;
+      if (!FAST && 4u * ql >= nc) break;
+      uint32_t r[4 * D];
+      gen_quad<D, FAST>(quad0 + ql, base_lo0 + 32u * D * j, base_hi, sid, rk, r);
+      float f[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) f[t] = ev(r + t * D);
-    if (j == 0) K = f[0];
+      for (int t = 0; t < 4; ++t) f[t] = ev(r + t * D);
+      if (j == jb) K = f[0];
+      if (FAST) {
+        s1 += (f[0] + f[1]) + (f[2] + f[3]);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (FAST || 4u * ql + t < nc) {
-        const float dlt = f[t] - K;
-        s1 += dlt;
-        s2 = fmaf(dlt, dlt, s2);
-        if (!FAST) ++cnt;
+        for (int t = 0; t < 4; ++t) {
+          const float dlt = f[t] - K;
+          s2 = fmaf(dlt, dlt, s2);
+        }
+      } else {
+        float q[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const bool ok = 4u * ql + t < nc;
+          q[t] = ok ? f[t] : 0.0f;
+          const float dlt = ok ? f[t] - K : 0.0f;
+          s2 = fmaf(dlt, dlt, s2);
+          cnt += ok ? 1u : 0u;
+        }
+        s1 += (q[0] + q[1]) + (q[2] + q[3]);
       }
     }
-  }
-  float n = FAST ? static_cast<float>(4u * Q) : static_cast<float>(cnt);
-  float mean = 0.0f, m2 = 0.0f;
-  if (n > 0.0f) {
-    const float avg = __fdiv_rn(s1, n);
-    mean = K + avg;
-    m2 = fmaxf(fmaf(-s1, avg, s2), 0.0f);
+    const float nb = FAST ? static_cast<float>(4u * (je - jb)) : static_cast<float>(cnt);
+    if (nb > 0.0f) {
+      const float mb = __fdiv_rn(s1, nb);
+      const float dk = mb - K;
+      const float m2b = fmaxf(fmaf(-nb * dk, dk, s2), 0.0f);
+      const float nab = n + nb;
+      const float delta = mb - mean;
+      const float wb = __fdiv_rn(nb, nab);
+      mean = fmaf(delta, wb, mean);
+      m2 = m2 + m2b + delta * delta * (n * wb);
+      n = nab;
+    }
+    if (!FAST && cnt < 4u * (je - jb)) break;
   }
   warp_chan_merge(n, mean, m2);
   if (lane == 0) fn->rec[chunk] = make_float2(mean, m2);

@@ -212,7 +212,25 @@ def test_plan_replay_is_bit_identical(zctx):
 def test_chunk_length_changes_only_rounding():
     tab = W.random_table(30, np.random.default_rng(4), n_lo=100, n_hi=40000)
     want, _ = oracle.integrate(tab)
-    for q in (1, 4, 64):
+    for q in (1, 4, 64, 256):
+        with zmc.Context(arena_bytes=256 << 20, quads_per_lane=q) as c:
+            got = zmc.zmc_integrate(c.handle, tab)
+        G.compare(tab, got, want)
+
+
+def test_peaked_integrands_long_chunks():
+    """Narrow Gaussians whose few large samples dominate the mean: the FP32 lane
+    sums must not let a large first sample inflate the rounding error."""
+    rng = np.random.default_rng(44)
+    tab = W.empty(48)
+    for i in range(48):
+        d = 1 + i % 7
+        lo = rng.uniform(-1, 0, size=d)
+        hi = lo + rng.uniform(0.5, 2, size=d)
+        W.gauss(tab[i], 1.0, rng.uniform(0.05, 0.2), rng.uniform(lo, hi), lo, hi,
+                int(rng.integers(3000, 60000)), seed=i, stream_id=i)
+    want, _ = oracle.integrate(tab)
+    for q in (16, 64, 256):
         with zmc.Context(arena_bytes=256 << 20, quads_per_lane=q) as c:
             got = zmc.zmc_integrate(c.handle, tab)
         G.compare(tab, got, want)
