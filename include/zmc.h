@@ -208,6 +208,35 @@ zmc_status zmc_philox4x32_10(zmc_ctx *ctx, const uint32_t *ctr, const uint32_t *
 zmc_status zmc_eval_samples(zmc_ctx *ctx, const zmc_desc *desc, uint64_t s_begin,
                             uint32_t count, float *out);
 
+/* ---- Integration without allocation (the paper has no counterpart) -------------
+ * For callers that must not allocate device memory when they need a result: a
+ * framework whose pool owns all device memory and forbids side allocations, a
+ * latency-bound loop that cannot take an allocation's implicit synchronisation
+ * or its failure on a nearly full device, or code that cannot create a context
+ * (zmc_create allocates an arena).
+ *
+ * zmc_integrate_noalloc computes what zmc_integrate computes for desc[0..n) (host
+ * array) and writes the n results to `out`, a DEVICE array the caller owns.  It
+ * is asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream) on
+ * the current device: read `out` after synchronising the stream.  It needs no
+ * context and allocates nothing: its launch header, work list, device
+ * descriptors and partial sums live in one fixed array of
+ * ZMC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   - At most ZMC_NOALLOC_MAX_FNS integrands (ZMC_EINVAL beyond) and at most
+ *     ~4e9 samples in total at 2048 samples per chunk (ZMC_ENOMEM beyond, with
+ *     the needed size in zmc_last_error()).
+ *   - All calls share the array and it keeps the previous call's contents; each
+ *     call re-uploads its tables and zeroes its work counters.  Calls whose GPU
+ *     work overlaps (other streams, or unordered host threads) race: order them.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make it before any stream capture.
+ *   - Results equal zmc_integrate's with the default quads_per_lane (16).      */
+#define ZMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define ZMC_NOALLOC_MAX_FNS 4096u
+zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_result *out,
+                                 void *stream);
+
 /* Host-only check of n descriptors with the rules listed at zmc_desc (no GPU
  * needed).  Returns ZMC_OK, or ZMC_EINVAL with *bad_index (if non-NULL) set to
  * the first rejected row. */

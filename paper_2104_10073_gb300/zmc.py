@@ -84,6 +84,7 @@ _SIGS = {
     "zmc_philox4x32_10": ([_P, _P, _P, _P, ctypes.c_size_t], ctypes.c_int),
     "zmc_eval_samples": ([_P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_validate": ([_P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "zmc_integrate_noalloc": ([_P, ctypes.c_size_t, _P, _P], ctypes.c_int),
     "zmc_desc_size": ([], ctypes.c_size_t),
     "zmc_result_size": ([], ctypes.c_size_t),
 }
@@ -244,6 +245,14 @@ def zmc_eval_samples(ctx: int, row, s_begin: int, count: int) -> np.ndarray:
     _check(lib().zmc_eval_samples(ctx, t.ctypes.data, int(s_begin), int(count),
                                   out.ctypes.data), "zmc_eval_samples")
     return out
+
+
+def zmc_integrate_noalloc(desc, out_device_ptr: int, stream_ptr: int | None) -> int:
+    """Status of one call of the no-allocation entry point: ``desc`` stays on the
+    host, results go to the caller's device array ``out_device_ptr`` (n rows of
+    32 bytes) asynchronously on ``stream_ptr``; nothing is allocated."""
+    t = _table(desc)
+    return lib().zmc_integrate_noalloc(t.ctypes.data, len(t), out_device_ptr, stream_ptr)
 
 
 def zmc_validate(desc):
