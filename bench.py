@@ -49,6 +49,38 @@ def harmonic_ops_per_sample(d: int) -> int:
     return 10 * d + 3 * d + 6 + 10 + 8 + 3
 
 
+KERNEL_SOURCES = ["paper_2104_10073_gb300/csrc/zmc_kernels.cu",
+                  "paper_2104_10073_gb300/csrc/zmc_internal.h",
+                  "paper_2104_10073_gb300/csrc/zmc_coeffs.h"]
+PROFILE = os.path.join(ROOT, "profiles", "zmc_batched_harmonic_fig1x10.md")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_counters():
+    """DRAM traffic and pipe utilisation of the dominant kernel from the committed
+    ncu summary, only if it was taken from the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    start = text.find("```json")
+    if start < 0:
+        return None
+    end = text.find("```", start + 7)
+    prof = json.loads(text[start + 7:end])
+    if prof.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    return prof
+
+
 class ClockSampler:
     """nvidia-smi SM clock / throttle-reason samples while the timed region runs."""
 
@@ -225,10 +257,11 @@ def run_native(args, world, rank, local):
     # CPU baseline first (host threads only; no process is forked after CUDA init)
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        sample = W.harmonic_fig1(10**6, seeds=[0])
+        sample = W.harmonic_fig1(10**6, seeds=range(args.cpu_repeats))
         rate, used, dt = oracle_rate(sample)
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
-               "sample": f"Fig. 1 harmonics, key 0, 100 x 1e6 samples ({dt:.1f} s)"}
+               "sample": f"Fig. 1 harmonics, keys 0..{args.cpu_repeats - 1}, "
+                         f"{len(sample)} x 1e6 samples ({dt:.1f} s wall)"}
 
     ctx = zmc.Context(arena_bytes=2 << 30, device=local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
@@ -320,6 +353,7 @@ def run_native(args, world, rank, local):
     peak_gops = sms * 128 * sm_clock * 1e6 / 1e9
     ops = harmonic_ops_per_sample(4) * n_samples
     achieved = ops / (kms / 1e3) / 1e9
+    prof = profile_counters()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -341,11 +375,13 @@ def run_native(args, world, rank, local):
             "d2h_bytes_per_step": len(tab) * 32,
             "path": "zmc_integrate (host table in, host results out)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved / peak_gops, "traffic": None,
+                     "frac": achieved / peak_gops,
+                     "traffic": prof["dram_bytes_per_launch"] if prof else None,
                      "kernel": "zmc_batched_kernel<HARMONIC>",
                      "kernel_ms": kms,
-                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz issue",
-                     "ops_per_sample": harmonic_ops_per_sample(4)},
+                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz issue slots",
+                     "ops_per_sample": harmonic_ops_per_sample(4),
+                     "ncu_pipes": prof["pipes"] if prof else None},
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
@@ -404,13 +440,14 @@ def run_serving(zmc, device, rate_hz, seconds):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-mixed", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--cpu-repeats", type=int, default=10)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=100.0)
     ap.add_argument("--serving-seconds", type=float, default=10.0)

@@ -200,12 +200,55 @@ def mixed(n_fn: int = 10**4, gen_seed: int = 2104, seed: int = 0,
     return t
 
 
+def mixed_block(rng, n_fn: int, seed: int, lo_exp: float = 4.0, hi_exp: float = 7.0,
+                stream_base: int = 0) -> np.ndarray:
+    """``n_fn`` rows drawn like :func:`mixed`, vectorised (same distributions,
+    drawn array by array, so the rows differ from :func:`mixed`'s)."""
+    t = empty(n_fn)
+    fam = rng.integers(0, 4, size=n_fn)
+    dim = rng.integers(1, MAX_DIM + 1, size=n_fn)
+    t["family"] = fam
+    t["dim"] = dim
+    t["stream_id"] = stream_base + np.arange(n_fn)
+    t["seed"] = seed
+    t["n_samples"] = np.round(10.0 ** rng.uniform(lo_exp, hi_exp, size=n_fn)).astype(np.uint64)
+    active = np.arange(MAX_DIM)[None, :] < dim[:, None]
+    lo = rng.uniform(-1.0, 0.0, size=(n_fn, MAX_DIM))
+    hi = lo + rng.uniform(0.5, 2.0, size=(n_fn, MAX_DIM))
+    t["lo"] = np.where(active, lo, 0.0)
+    t["hi"] = np.where(active, hi, 0.0)
+    p = np.zeros((n_fn, N_PARAM))
+    ab = rng.uniform(0.5, 2.0, size=(n_fn, 2))
+    k = rng.uniform(-30.0, 30.0, size=(n_fn, MAX_DIM))
+    c = rng.choice([-1.0, 1.0], size=(n_fn, MAX_DIM))
+    sigma = rng.uniform(0.05, 0.5, size=n_fn)
+    mu = rng.uniform(lo, hi)
+    deg = rng.integers(0, 5, size=n_fn)
+    coef = rng.standard_normal(size=(n_fn, MAX_DIM, 5))
+    h = fam == HARMONIC
+    p[h, 0], p[h, 1] = ab[h, 0], ab[h, 1]
+    p[h, 2:2 + MAX_DIM] = np.where(active[h], k[h], 0.0)
+    a = fam == ABSLIN
+    p[a, 0] = ab[a, 0]
+    p[a, 1:1 + MAX_DIM] = np.where(active[a], c[a], 0.0)
+    g = fam == GAUSS
+    p[g, 0], p[g, 1] = 1.0, sigma[g]
+    p[g, 2:2 + MAX_DIM] = np.where(active[g], mu[g], 0.0)
+    q = fam == POLY
+    mask = active[:, :, None] & (np.arange(5)[None, None, :] <= deg[:, None, None])
+    p[q, :5 * MAX_DIM] = np.where(mask[q], coef[q], 0.0).reshape(-1, 5 * MAX_DIM)
+    t["p"] = p
+    t["deg"] = np.where(q, deg, 0)
+    return t
+
+
 def serving_stream(rate_hz: float, duration_s: float, arrival_seed: int = 5,
                    max_fns: int = 1000, lo_exp: float = 4.0, hi_exp: float = 7.0):
     """Poisson job arrivals at ``rate_hz`` over ``duration_s`` seconds.
 
     Returns a list of (arrival_time_s, table).  Each job holds U{1..max_fns}
-    integrands drawn like :func:`mixed`, with the job index as Philox key.
+    integrands drawn like :func:`mixed` (by :func:`mixed_block`), with the job
+    index as Philox key.
     """
     rng = np.random.default_rng(arrival_seed)
     jobs = []
@@ -217,10 +260,7 @@ def serving_stream(rate_hz: float, duration_s: float, arrival_seed: int = 5,
             break
         n_fn = int(rng.integers(1, max_fns + 1))
         jr = np.random.default_rng([arrival_seed, j])
-        tab = empty(n_fn)
-        for i in range(n_fn):
-            _mixed_row(jr, tab[i], log_uniform_budget(jr, lo_exp, hi_exp), j, i)
-        jobs.append((t, tab))
+        jobs.append((t, mixed_block(jr, n_fn, seed=j, lo_exp=lo_exp, hi_exp=hi_exp)))
         j += 1
     return jobs
 
