@@ -1,12 +1,8 @@
 """Fit the FP32 polynomials the kernels evaluate instead of library calls.
 
-* sin(2 pi t), cos(2 pi t) on |t| <= 1/8 turn.  The kernels reduce every phase
-  to a quarter-turn index q and a remainder t in [-1/8, 1/8] turns (exactly, in
-  fixed point), then evaluate
-      sin(2 pi t) ~= t * (S0 + S1 t^2 + S2 t^4 + S3 t^6)
-      cos(2 pi t) ~= C0 + C1 t^2 + C2 t^4 + C3 t^6 + C4 t^8
-  fitted in the variable z = t^2 (absolute error for cos; the error of
-  sin(2 pi t)/t weighted by |t| for sin).
+* cos(2 pi t) on 0 <= t <= 1/4 (+2^-24) turn, degree 5 in z = t^2 (absolute
+  error): the harmonic family reduces its fixed-point phase to |t| <= 1/4 turn
+  by the symmetries of cosine and evaluates R cos(2 pi t).
 * 2^x on |x| <= 0.51 (relative error), degree 6: the Gaussian family's
   2^-Z = 2^-n 2^-r after n = rint(Z).
 
@@ -22,11 +18,7 @@ import mpmath
 import numpy as np
 
 mpmath.mp.dps = 50
-T_MAX = mpmath.mpf(1) / 8
-Z_MAX = T_MAX**2
-
-
-def remez(target, weight, n_coef, iters=30, a=mpmath.mpf(0), b=Z_MAX):
+def remez(target, weight, n_coef, a, b, iters=30):
     """Minimax polynomial p(z) = sum c_j z^j of weight(z) * (target(z) - p(z)) on [a, b]."""
     m = n_coef + 1
     # Chebyshev extrema as the first reference
@@ -68,44 +60,32 @@ def remez(target, weight, n_coef, iters=30, a=mpmath.mpf(0), b=Z_MAX):
     return coef
 
 
-def sin_target(z):
-    t = mpmath.sqrt(z)
-    if t == 0:
-        return 2 * mpmath.pi
-    return mpmath.sin(2 * mpmath.pi * t) / t
-
-
 def main():
-    s = remez(sin_target, lambda z: mpmath.sqrt(z) if z > 0 else mpmath.mpf("1e-30"), 4)
-    c = remez(lambda z: mpmath.cos(2 * mpmath.pi * mpmath.sqrt(z)), lambda z: 1, 5)
-    s32 = [np.float32(float(v)) for v in s]
-    c32 = [np.float32(float(v)) for v in c]
-    t = np.linspace(-1 / 8, 1 / 8, 200001)
+    zq = (mpmath.mpf(1) / 4 + mpmath.mpf(2) ** -24) ** 2
+    cq = remez(lambda z: mpmath.cos(2 * mpmath.pi * mpmath.sqrt(z)), lambda z: 1, 6,
+               mpmath.mpf(0), zq)
+    cq32 = [np.float32(float(v)) for v in cq]
+    t = np.linspace(0, 0.25 + 2.0**-24, 200001)
     z = t * t
-    ps = t * sum(float(v) * z**j for j, v in enumerate(s32))
-    pc = sum(float(v) * z**j for j, v in enumerate(c32))
-    es = np.max(np.abs(ps - np.sin(2 * np.pi * t)))
+    pc = sum(float(v) * z**j for j, v in enumerate(cq32))
     ec = np.max(np.abs(pc - np.cos(2 * np.pi * t)))
     xm = mpmath.mpf("0.51")
-    e2 = remez(lambda x: mpmath.power(2, x), lambda x: 1 / mpmath.power(2, x), 7, a=-xm, b=xm)
+    e2 = remez(lambda x: mpmath.power(2, x), lambda x: 1 / mpmath.power(2, x), 7, -xm, xm)
     e32 = [np.float32(float(v)) for v in e2]
     x = np.linspace(-0.51, 0.51, 200001)
     pe = sum(float(v) * x**j for j, v in enumerate(e32))
     ee = np.max(np.abs(pe / np.exp2(x) - 1))
-    print(f"max |sin err| {es:.3e}  max |cos err| {ec:.3e}  max |exp2 rel err| {ee:.3e}")
+    print(f"max |cos err| {ec:.3e}  max |exp2 rel err| {ee:.3e}")
     here = os.path.dirname(os.path.abspath(__file__))
     lines = [
         "// Generated by gen_coeffs.py: Remez fits rounded to binary32.  Max error of the",
         "// rounded polynomials in exact arithmetic:",
-        f"//   sin(2 pi t), |t| <= 1/8 (in t^2): {es:.2e} absolute",
-        f"//   cos(2 pi t), |t| <= 1/8 (in t^2): {ec:.2e} absolute",
+        f"//   cos(2 pi t), 0 <= t <= 1/4 (degree 5 in t^2): {ec:.2e} absolute",
         f"//   2^x, |x| <= 0.51, degree 6:       {ee:.2e} relative",
         "#pragma once",
     ]
-    for j, v in enumerate(s32):
-        lines.append(f"#define ZMC_SIN_C{j} {float(v).hex()}f  // {float(v):.9e}")
-    for j, v in enumerate(c32):
-        lines.append(f"#define ZMC_COS_C{j} {float(v).hex()}f  // {float(v):.9e}")
+    for j, v in enumerate(cq32):
+        lines.append(f"#define ZMC_COSQ_C{j} {float(v).hex()}f  // {float(v):.9e}")
     for j, v in enumerate(e32):
         lines.append(f"#define ZMC_EXP2_C{j} {float(v).hex()}f  // {float(v):.9e}")
     with open(os.path.join(here, "zmc_coeffs.h"), "w") as f:

@@ -36,9 +36,12 @@ __host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t di
 // constant split as hi = fl32(c), lo = fl32(c - hi), so that FMA chains over
 // both halves carry the constant to ~2^-48 relative).  m_i = word & 0x7FFFFF is
 // the 23-bit sample integer of coordinate i, u_i = m_i 2^-23, v_i = 1 + u_i.
-//   HARMONIC  T_i (u64 two's complement) at w[2i], i < 7: k_i (hi_i-lo_i)/(2 pi) * 2^41,
-//             i.e. turns per unit of m_i, in units of 2^-64 turn;
-//             P0 (u64) at w[14]: frac(k.lo/(2 pi)) * 2^64;  S a w[16], S b w[17], -S a w[18].
+//   HARMONIC  f = S R cos(2 pi P), P = k.x/(2 pi) - atan2(b, a)/(2 pi) in turns,
+//             R = sqrt(a^2 + b^2); T_i = k_i (hi_i-lo_i)/(2 pi) 2^41 (turns per
+//             unit of m_i, in units of 2^-64 turn): high word at w[i] (u32),
+//             fl32(low word / 2^32) at w[7+i], fl32(2^23 - w[7+i] 2^23) at w[14+i];
+//             P0 (u32, units of 2^-32 turn, minus the folded 2^23 offsets) w[21];
+//             S R at w[22].
 //   ABSLIN    s = C + sum_i g_i v_i:  g_i = c_i (hi_i - lo_i): hi w[i], lo w[7+i];
 //             C = sum_i c_i (lo_i - (hi_i - lo_i)): hi w[14], lo w[15];  S a w[16].
 //   GAUSS     t_i = (x_i - mu_i) beta, beta = sqrt(log2(e) / 2) / sigma, so that

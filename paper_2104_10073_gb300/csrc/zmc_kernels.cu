@@ -135,44 +135,57 @@ __device__ __forceinline__ float amp_exp2_neg(float amp, float zh, float zl) {
 template <int FAM, int D, int G>
 struct Eval;
 
-// a cos(k.x) + b sin(k.x) (Eq. 1).  The phase k.x / (2 pi) is formed exactly in
-// 64-bit fixed point (units of 2^-64 turn) from the 23-bit sample integers, so
-// its fraction is exact however large |k.x| is; the quarter-turn index q and the
-// remainder t in [-1/8, 1/8] turn come from integer bit fields; sin and cos of
-// 2 pi t are short polynomials; the quadrant rotates (a, b).
+// a cos(k.x) + b sin(k.x) (Eq. 1) = R cos(2 pi P), R = sqrt(a^2 + b^2), with the
+// phase P in turns = k.x / (2 pi) - atan2(b, a) / (2 pi).  P's fraction is kept
+// as a 32-bit fixed-point number (units of 2^-32 turn), formed from the 23-bit
+// sample integers m_i: P = P0 + sum_i [T_hi,i m_i + round(T_lo,i m_i / 2^32)],
+// where T_i = k_i (hi_i - lo_i) / (2 pi) 2^41 is split into its high and low
+// 32-bit words.  The high-word products wrap modulo 1 turn exactly (one 32-bit
+// multiply-add each); the low-word contribution (< 2^23 units) is formed by one
+// FP32 FMA from v' = 2^23 + m_i, whose rounding and the dropped carries cost at
+// most D units of 2^-32 turn.  So |k.x| of any size costs no accuracy.  Then
+// cos is reduced by symmetry to |t| <= 1/4 turn (sign from the half of the
+// period) and evaluated by a degree-5 polynomial in t^2.
 template <int D, int G>
 struct Eval<ZMC_HARMONIC, D, G> {
-  uint64_t T[D];
-  uint64_t P0;
-  float a, b, na;
+  uint32_t thi[D];
+  float tlo[D], kc[D];
+  uint32_t p0;
+  float R;
   __device__ __forceinline__ void load(const FnDev *fn) {
-    const uint64_t *w64 = reinterpret_cast<const uint64_t *>(fn->w);
 #pragma unroll
-    for (int i = 0; i < D; ++i) T[i] = w64[i];
-    P0 = w64[7];
-    a = __uint_as_float(fn->w[16]);
-    b = __uint_as_float(fn->w[17]);
-    na = __uint_as_float(fn->w[18]);
+    for (int i = 0; i < D; ++i) {
+      thi[i] = fn->w[i];
+      tlo[i] = __uint_as_float(fn->w[7 + i]);
+      kc[i] = __uint_as_float(fn->w[14 + i]);
+    }
+    p0 = fn->w[21];
+    R = __uint_as_float(fn->w[22]);
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
-    uint64_t acc = P0;
+    uint32_t acc = p0;
 #pragma unroll
-    for (int i = 0; i < D; ++i) acc += T[i] * static_cast<uint64_t>(r[i] & 0x7FFFFFu);
-    const uint32_t g = static_cast<uint32_t>(acc >> 32) + 0x20000000u;  // + 1/8 turn
-    const uint32_t q = g >> 30;                                          // nearest quarter
-    // bits 7..29 of g: the remainder (+1/8) truncated to 2^-25 turn, as 2^23 + Y
-    const float yf = __fsub_rn(__uint_as_float(((g >> 7) & 0x7FFFFFu) | 0x4B000000u), 12582912.0f);
-    const float t = fmaf(yf, 0x1p-25f, 0x1p-26f);  // midpoint of the truncated bits
+    for (int i = 0; i < D; ++i) {
+      const uint32_t vb = (r[i] & 0x7FFFFFu) | 0x4B000000u;  // bits of 2^23 + m_i
+      const float c = fmaf(tlo[i], __uint_as_float(vb), kc[i]);
+      acc = thi[i] * vb + acc + __float_as_uint(c);  // host folds the 0x4B000000 terms
+    }
+    // x = acc / 2^32 in [-1/2, 1/2) turn; cos(2 pi x) = sign cos(2 pi a'),
+    // a' = 1/4 - | |x| - 1/4 | in [0, 1/4] (units of 2^-32 turn)
+    const int32_t ax = abs(static_cast<int32_t>(acc));
+    const int32_t d = 0x40000000 - ax;
+    const uint32_t ap = static_cast<uint32_t>(0x40000000 - abs(d));
+    const uint32_t sign = static_cast<uint32_t>(d) & 0x80000000u;
+    // ap truncated to 2^-25 turn as the float 2^23 + (ap >> 7); midpoint restored
+    const float yf = __fsub_rn(__uint_as_float((ap >> 7) | 0x4B000000u), 8388608.0f);
+    const float t = fmaf(yf, 0x1p-25f, 0x1p-26f);
     const float z = t * t;
-    const float s =
-        t * fmaf(fmaf(fmaf(ZMC_SIN_C3, z, ZMC_SIN_C2), z, ZMC_SIN_C1), z, ZMC_SIN_C0);
-    const float c = fmaf(fmaf(fmaf(fmaf(ZMC_COS_C4, z, ZMC_COS_C3), z, ZMC_COS_C2), z,
-                              ZMC_COS_C1), z, ZMC_COS_C0);
-    const bool odd = (q & 1u) != 0u;
-    const uint32_t flip = (q & 2u) << 30;
-    const float A = __uint_as_float(__float_as_uint(odd ? b : a) ^ flip);
-    const float B = __uint_as_float(__float_as_uint(odd ? na : b) ^ flip);
-    return fmaf(A, c, B * s);
+    float p = fmaf(ZMC_COSQ_C5, z, ZMC_COSQ_C4);
+    p = fmaf(p, z, ZMC_COSQ_C3);
+    p = fmaf(p, z, ZMC_COSQ_C2);
+    p = fmaf(p, z, ZMC_COSQ_C1);
+    p = fmaf(p, z, ZMC_COSQ_C0);
+    return __uint_as_float(__float_as_uint(R) ^ sign) * p;
   }
 };
 

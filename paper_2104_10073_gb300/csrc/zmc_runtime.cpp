@@ -199,24 +199,32 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
   bool ok = true;
   switch (d.family) {
     case ZMC_HARMONIC: {
-      // phase in turns = k.lo/(2 pi) + sum_i [k_i w_i / (2 pi)] m_i 2^-23
-      double phi = 0.0;
-      uint64_t *w64 = reinterpret_cast<uint64_t *>(fn->w);
+      // f = R cos(2 pi P): R = S sqrt(a^2+b^2), P = k.x/(2 pi) - atan2(b,a)/(2 pi)
+      // in turns; k.x/(2 pi) = k.lo/(2 pi) + sum_i [k_i w_i / (2 pi)] m_i 2^-23.
+      double phi = -std::atan2(p[1], p[0]) / kTwoPi;
+      uint32_t fold = 0;  // the 2^23 offsets the kernel adds, removed from P0
       for (int i = 0; i < dim; ++i) {
         const double tau = p[2 + i] * w[i] / kTwoPi;
         if (!(std::fabs(tau) <= 1048576.0))
           return set_error(ZMC_EINVAL, "harmonic |k_i (hi_i-lo_i)| / 2pi above 2^20 turns");
-        const long long T = std::llround(std::ldexp(tau, 41));
-        w64[i] = static_cast<uint64_t>(T);
+        const uint64_t T = static_cast<uint64_t>(std::llround(std::ldexp(tau, 41)));
+        const uint32_t thi = static_cast<uint32_t>(T >> 32);
+        const double tlo = std::ldexp(static_cast<double>(static_cast<uint32_t>(T)), -32);
+        const float tlo_f = static_cast<float>(tlo);
+        const float kc = static_cast<float>(8388608.0 - static_cast<double>(tlo_f) * 8388608.0);
+        fn->w[i] = thi;
+        std::memcpy(&fn->w[7 + i], &tlo_f, 4);
+        std::memcpy(&fn->w[14 + i], &kc, 4);
+        fold += (thi + 1u) * 0x4B000000u;
         phi += p[2 + i] * d.lo[i] / kTwoPi;
       }
       if (!(std::fabs(phi) < 4.0e15)) return set_error(ZMC_EINVAL, "harmonic phase too large");
       const double fr = phi - std::floor(phi);  // exact, in [0, 1)
-      w64[7] = static_cast<uint64_t>(std::ldexp(fr, 64));
-      ok = finite_f32(S * p[0]) && finite_f32(S * p[1]);
-      put_f32(&fn->w[16], S * p[0]);
-      put_f32(&fn->w[17], S * p[1]);
-      put_f32(&fn->w[18], -S * p[0]);
+      const uint32_t p0 = static_cast<uint32_t>(static_cast<uint64_t>(std::ldexp(fr, 64)) >> 32);
+      fn->w[21] = p0 - fold;
+      const double R = S * std::hypot(p[0], p[1]);
+      ok = finite_f32(R);
+      put_f32(&fn->w[22], R);
       break;
     }
     case ZMC_ABSLIN: {

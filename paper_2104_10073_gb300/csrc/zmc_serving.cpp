@@ -13,12 +13,17 @@
 //      event; two iteration slots are in flight at once;
 //   4. when a slot's event completes, hand the finished jobs' results to
 //      zmc_poll and free their device blocks.
+// Failures: a failed CUDA call in the loop poisons the context, every pending job
+// completes with ZMC_ECUDA and later calls on the context return ZMC_ECUDA.  The
+// environment variable ZMC_SERVING_FAULT_AT=<k> injects such a failure on the
+// host at iteration k (for tests; no GPU fault is involved).
 // A chunk's record depends only on (integrand, chunk) and the merge sums records
 // in a fixed order, so a job's results are bit-identical whether it runs alone or
 // mixed with others.  No kernel waits on another: every launch drains a finite
 // work list and exits.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 
 #include "zmc_runtime.h"
@@ -89,6 +94,7 @@ struct ServingState {
   uint64_t seq = 0;
   zmc_serving_stats stats{};
   zmc_status thread_status = ZMC_OK;
+  uint64_t fault_at = 0;  // host-side fault injection (tests): iteration that fails
 };
 
 namespace {
@@ -362,6 +368,13 @@ void scheduler_loop(ServingState *S) {
     const size_t mrg_bytes = round256(S->max_merge * sizeof(FnDev *));
     const size_t hdr_bytes = round256(sizeof(LaunchHdr));
     cudaError_t e = cudaSuccess;
+    if (S->fault_at != 0 && seq == S->fault_at) {
+      // injected on the host: nothing of this iteration is enqueued, and it is
+      // reported exactly like a failed CUDA call
+      ctx_cuda_fail(ctx, cudaErrorLaunchFailure, "serving iteration (injected fault)");
+      S->thread_status = ZMC_ECUDA;
+      continue;
+    }
     if (k > 0)
       e = cudaMemcpyAsync(slot->d_entries, ents, k * sizeof(Entry), cudaMemcpyHostToDevice,
                           S->stream);
@@ -397,6 +410,7 @@ zmc_status serving_start(zmc_ctx *ctx) {
   S->max_entries = std::max<uint32_t>(S->max_chunks, 1024);
   S->max_entries = std::min<uint32_t>(S->max_entries, 1u << 20);
   S->max_merge = 1u << 16;
+  if (const char *f = std::getenv("ZMC_SERVING_FAULT_AT")) S->fault_at = std::strtoull(f, nullptr, 10);
   cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving stream");
   for (int f = 0; f < 4; ++f) S->grid[f] = family_grid(ctx, f, ~0ull >> 8);

@@ -190,6 +190,20 @@ def test_results_independent_of_batch_composition(zctx):
         assert np.array_equal(part["stderr"], full["stderr"][sl], equal_nan=True)
 
 
+def test_row_partition_through_the_library(zctx):
+    """Whole integrands split over ranks (run here one after another) and gathered
+    back reproduce the single call bit for bit."""
+    from paper_2104_10073_gb300 import shard
+
+    tab = W.mixed(120, gen_seed=12, lo_exp=3.0, hi_exp=5.5)
+    full = zmc.zmc_integrate(zctx.handle, tab)
+    est = np.full(len(tab), np.nan)
+    for rows in shard.partition_rows(tab, 3):
+        part = zmc.zmc_integrate(zctx.handle, tab[rows])
+        est[rows] = part["estimate"]
+    assert np.array_equal(est, full["estimate"])
+
+
 def test_plan_replay_is_bit_identical(zctx):
     tab = W.mixed(200, gen_seed=3, lo_exp=3, hi_exp=5)
     plan = zmc.zmc_plan_create(zctx.handle, tab)

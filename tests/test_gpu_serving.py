@@ -135,3 +135,25 @@ def test_poisson_stream_latency_recorded(sctx):
         assert st == zmc.ZMC_OK
         lat.append(time.perf_counter() - ts)
     assert max(lat) < 60.0 and time.perf_counter() - t0 < 120.0
+
+
+def test_injected_iteration_failure_poisons_context(monkeypatch):
+    """A failure injected on the host at the first iteration fails the pending
+    jobs with ZMC_ECUDA, poisons the context, and leaves the GPU usable."""
+    monkeypatch.setenv("ZMC_SERVING_FAULT_AT", "1")
+    c = zmc.Context(arena_bytes=128 << 20, serving=True)
+    monkeypatch.delenv("ZMC_SERVING_FAULT_AT")
+    try:
+        t = W.harmonic_fig1(2000)[:10]
+        jid = zmc.zmc_submit(c.handle, t)
+        st, res = zmc.zmc_poll(c.handle, jid, len(t), wait_ms=30000)
+        assert st == zmc.ZMC_ECUDA and res is None
+        with pytest.raises(zmc.ZmcError) as e:
+            zmc.zmc_integrate(c.handle, t)
+        assert e.value.status == zmc.ZMC_ECUDA
+    finally:
+        c.close()
+    with zmc.Context(arena_bytes=64 << 20) as ok:
+        got = zmc.zmc_integrate(ok.handle, t)
+    want, _ = oracle.integrate(t)
+    G.compare(t, got, want)
