@@ -1,10 +1,9 @@
 """Fit the FP32 polynomials the kernels evaluate instead of library calls.
 
-* cos(2 pi t) on 0 <= t <= 1/4 (+2^-24) turn, degree 5 in z = t^2 (absolute
-  error): the harmonic family reduces its fixed-point phase to |t| <= 1/4 turn
-  by the symmetries of cosine and evaluates R cos(2 pi t).
-* 2^x on |x| <= 0.51 (relative error), degree 6: the Gaussian family's
-  2^-Z = 2^-n 2^-r after n = rint(Z).
+* sin(2 pi t) / t on |t| <= 1/4 turn, degree 5 in z = t^2 (relative error):
+  the harmonic family writes cos(2 pi x) = sin(2 pi (1/4 - |x|)) for its
+  fixed-point phase x in [-1/2, 1/2) turn and evaluates R t P(t^2), which keeps
+  the relative accuracy near the zeros.
 
 Every fit is a Remez exchange carried out in 50-digit arithmetic, then rounded to
 binary32.  The script prints the maximum error of the rounded polynomials
@@ -61,33 +60,28 @@ def remez(target, weight, n_coef, a, b, iters=30):
 
 
 def main():
-    zq = (mpmath.mpf(1) / 4 + mpmath.mpf(2) ** -24) ** 2
-    cq = remez(lambda z: mpmath.cos(2 * mpmath.pi * mpmath.sqrt(z)), lambda z: 1, 6,
-               mpmath.mpf(0), zq)
-    cq32 = [np.float32(float(v)) for v in cq]
-    t = np.linspace(0, 0.25 + 2.0**-24, 200001)
+    zq = (mpmath.mpf(1) / 4) ** 2
+
+    def sinc2(z):
+        t = mpmath.sqrt(z)
+        return 2 * mpmath.pi if t == 0 else mpmath.sin(2 * mpmath.pi * t) / t
+
+    sq = remez(sinc2, lambda z: 1 / sinc2(z), 6, mpmath.mpf(0), zq)
+    sq32 = [np.float32(float(v)) for v in sq]
+    t = np.linspace(1e-6, 0.25, 200001)
     z = t * t
-    pc = sum(float(v) * z**j for j, v in enumerate(cq32))
-    ec = np.max(np.abs(pc - np.cos(2 * np.pi * t)))
-    xm = mpmath.mpf("0.51")
-    e2 = remez(lambda x: mpmath.power(2, x), lambda x: 1 / mpmath.power(2, x), 7, -xm, xm)
-    e32 = [np.float32(float(v)) for v in e2]
-    x = np.linspace(-0.51, 0.51, 200001)
-    pe = sum(float(v) * x**j for j, v in enumerate(e32))
-    ee = np.max(np.abs(pe / np.exp2(x) - 1))
-    print(f"max |cos err| {ec:.3e}  max |exp2 rel err| {ee:.3e}")
+    ps = t * sum(float(v) * z**j for j, v in enumerate(sq32))
+    es = np.max(np.abs(ps / np.sin(2 * np.pi * t) - 1))
+    print(f"max |sin rel err| {es:.3e}")
     here = os.path.dirname(os.path.abspath(__file__))
     lines = [
         "// Generated by gen_coeffs.py: Remez fits rounded to binary32.  Max error of the",
         "// rounded polynomials in exact arithmetic:",
-        f"//   cos(2 pi t), 0 <= t <= 1/4 (degree 5 in t^2): {ec:.2e} absolute",
-        f"//   2^x, |x| <= 0.51, degree 6:       {ee:.2e} relative",
+        f"//   sin(2 pi t), |t| <= 1/4 (t times degree 5 in t^2): {es:.2e} relative",
         "#pragma once",
     ]
-    for j, v in enumerate(cq32):
-        lines.append(f"#define ZMC_COSQ_C{j} {float(v).hex()}f  // {float(v):.9e}")
-    for j, v in enumerate(e32):
-        lines.append(f"#define ZMC_EXP2_C{j} {float(v).hex()}f  // {float(v):.9e}")
+    for j, v in enumerate(sq32):
+        lines.append(f"#define ZMC_SINQ_C{j} {float(v).hex()}f  // {float(v):.9e}")
     with open(os.path.join(here, "zmc_coeffs.h"), "w") as f:
         f.write("\n".join(lines) + "\n")
 
