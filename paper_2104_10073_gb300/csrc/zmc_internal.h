@@ -42,14 +42,16 @@ __host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t di
 //             fl32(low word / 2^32) at w[7+i], fl32(2^23 - w[7+i] 2^23) at w[14+i];
 //             P0 (u32, units of 2^-32 turn, minus the folded 2^23 offsets) w[21];
 //             S R at w[22].
-//   ABSLIN    s = C + sum_i g_i v_i:  g_i = c_i (hi_i - lo_i): hi w[i], lo w[7+i];
-//             C = sum_i c_i (lo_i - (hi_i - lo_i)): hi w[14], lo w[15];  S a w[16].
+//   ABSLIN    s = C + sum_i g_i v_i:  g_i = fl32(c_i (hi_i - lo_i)) at w[i];
+//             C = sum_i c_i (lo_i - (hi_i - lo_i)) + 3/2 sum_i (g_i - fl32(g_i)):
+//             hi w[14], lo w[15];  S a w[16].
 //   GAUSS     t_i = (x_i - mu_i) beta, beta = sqrt(log2(e) / 2) / sigma, so that
 //             f = A 2^(-sum t_i^2);  h_i = (hi_i - lo_i) beta: hi w[i], lo w[7+i];
 //             S A w[28].  Variant degree 0 ("near": mu_i / box position within
-//             [-1, 2] box widths in every dimension): t_i = h_i (u_i - u0_i) + c0_i
-//             with u0_i the position rounded to a multiple of 2^-23 (w[14+i]), so
-//             u_i - u0_i is exact, and c0_i = -h_i (position - u0_i) (w[21+i]).
+//             [-1, 2] box widths in every dimension): t_i = h_i (v_i - 1 - u0_i) + c0_i
+//             with u0_i the position rounded to a multiple of 2^-22 and 1 + u0_i
+//             stored (w[14+i], exact), so v_i - (1 + u0_i) is exact, and
+//             c0_i = -h_i (position - u0_i) (w[21+i]).
 //             Variant degree 1 ("far"): t_i = e_i + h_i u_i, e_i = (lo_i - mu_i) beta:
 //             hi w[14+i], lo w[21+i].
 //   POLY      factor i re-expanded in u_i in [0, 1): q_i(u) = sum_j e_ij u^j;

@@ -181,30 +181,25 @@ struct Eval<ZMC_HARMONIC, D, G> {
   }
 };
 
-// a |c.x| (Eq. 2), as a |C + sum g_i v_i| with hi/lo constant pairs.
+// a |c.x| (Eq. 2), as a |C + sum g_i v_i|: the g_i are FP32 roundings of FP64
+// constants; C carries the FP64 C plus the mean over the box of the dropped
+// low parts (sum (g_i - fl(g_i)) * 3/2), which removes their systematic effect.
 template <int D, int G>
 struct Eval<ZMC_ABSLIN, D, G> {
-  float gh[D], gl[D];
+  float g[D];
   float ch, cl, a;
   __device__ __forceinline__ void load(const FnDev *fn) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      gh[i] = __uint_as_float(fn->w[i]);
-      gl[i] = __uint_as_float(fn->w[7 + i]);
-    }
+    for (int i = 0; i < D; ++i) g[i] = __uint_as_float(fn->w[i]);
     ch = __uint_as_float(fn->w[14]);
     cl = __uint_as_float(fn->w[15]);
     a = __uint_as_float(fn->w[16]);
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
-    float sh = ch, sl = cl;
+    float sh = ch;
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const float v = unit_v(r[i]);
-      sh = fmaf(gh[i], v, sh);
-      sl = fmaf(gl[i], v, sl);
-    }
-    return a * fabsf(sh + sl);
+    for (int i = 0; i < D; ++i) sh = fmaf(g[i], unit_v(r[i]), sh);
+    return a * fabsf(sh + cl);
   }
 };
 
@@ -236,13 +231,14 @@ struct Eval<ZMC_GAUSS, D, G> {
     float zh = 0.0f, zl = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      const float u = __fsub_rn(unit_v(r[i]), 1.0f);  // exact
       float th, tl;
       if (G == 0) {
-        const float d = __fsub_rn(u, pa[i]);  // exact: multiples of 2^-23, |d| < 2
+        // d = v - (1 + u0): exact, the result is a multiple of 2^-23 below 2 in size
+        const float d = __fsub_rn(unit_v(r[i]), pa[i]);
         th = __fmul_rn(hh[i], d);
         tl = __fadd_rn(fmaf(hh[i], d, -th), fmaf(hl[i], d, pb[i]));
       } else {
+        const float u = __fsub_rn(unit_v(r[i]), 1.0f);  // exact
         const float ph = __fmul_rn(hh[i], u);
         const float pl = fmaf(hh[i], u, -ph);
         const float s = __fadd_rn(pa[i], ph);  // TwoSum(e_hi, h_hi u)
@@ -257,9 +253,10 @@ struct Eval<ZMC_GAUSS, D, G> {
         zh = qh;
         zl = c;
       } else {
-        const float s = __fadd_rn(zh, qh);  // TwoSum(zh, qh)
-        const float bb = __fsub_rn(s, zh);
-        const float err = __fadd_rn(__fsub_rn(zh, __fsub_rn(s, bb)), __fsub_rn(qh, bb));
+        // Fast2Sum on (max, min): both terms are >= 0, so the larger goes first
+        const float big = fmaxf(zh, qh), small = fminf(zh, qh);
+        const float s = __fadd_rn(big, small);
+        const float err = __fsub_rn(small, __fsub_rn(s, big));
         zh = s;
         zl = __fadd_rn(zl, __fadd_rn(err, c));
       }
@@ -269,7 +266,9 @@ struct Eval<ZMC_GAUSS, D, G> {
 };
 
 // prod_i q_i(u_i), q_i re-expanded in u_i in [0, 1) on the host; Horner on the
-// hi coefficients plus Horner on the lo coefficients.
+// hi coefficients plus Horner on the lo coefficients (an FP64 coefficient split
+// as hi + lo).  The lo terms cannot be replaced by their mean: with few samples
+// and cancelling coefficients their fluctuation is visible at 1e-6.
 template <int D, int G>
 struct Eval<ZMC_POLY, D, G> {
   float ch[D][G + 1], cl[D][G + 1];

@@ -228,12 +228,15 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
       break;
     }
     case ZMC_ABSLIN: {
+      // s = C + sum g_i v_i (v_i in [1, 2)); the kernel uses fl32(g_i), so the
+      // mean 3/2 sum (g_i - fl32(g_i)) of the dropped parts goes into C
       double C = 0.0;
       for (int i = 0; i < dim; ++i) {
         const double g = p[1 + i] * w[i];
         ok = ok && finite_f32(g);
-        split(g, &fn->w[i], &fn->w[7 + i]);
-        C += p[1 + i] * (d.lo[i] - w[i]);
+        const float gf = static_cast<float>(g);
+        std::memcpy(&fn->w[i], &gf, 4);
+        C += p[1 + i] * (d.lo[i] - w[i]) + 1.5 * (g - static_cast<double>(gf));
       }
       ok = ok && finite_f32(C) && finite_f32(S * p[0]);
       split(C, &fn->w[14], &fn->w[15]);
@@ -255,9 +258,10 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
         ok = ok && finite_f32(h);
         split(h, &fn->w[i], &fn->w[7 + i]);
         if (near) {
-          const double u0 = std::ldexp(std::nearbyint(std::ldexp(pos[i], 23)), -23);
-          put_f32(&fn->w[14 + i], u0);                       // exact
-          put_f32(&fn->w[21 + i], -h * (pos[i] - u0));        // |.| <= h 2^-24
+          // 1 + mu's position rounded to 2^-22: exact in FP32 over [0, 3]
+          const double u0 = std::ldexp(std::nearbyint(std::ldexp(pos[i], 22)), -22);
+          put_f32(&fn->w[14 + i], 1.0 + u0);                  // exact
+          put_f32(&fn->w[21 + i], -h * (pos[i] - u0));        // |.| <= h 2^-23
         } else {
           const double e = (d.lo[i] - p[2 + i]) * beta;
           ok = ok && finite_f32(e);
