@@ -263,7 +263,11 @@ def run_native(args, world, rank, local):
                "sample": f"Fig. 1 harmonics, keys 0..{args.cpu_repeats - 1}, "
                          f"{len(sample)} x 1e6 samples ({dt:.1f} s wall)"}
 
-    ctx = zmc.Context(arena_bytes=2 << 30, device=local)
+    import tempfile
+
+    tune_path = os.path.join(tempfile.gettempdir(), f"zmc_tune_{os.getuid()}_{local}.json")
+    ctx = zmc.Context(arena_bytes=2 << 30, device=local, autotune=not args.no_autotune,
+                      tune_cache_path=tune_path)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     tab = fig1_table(rank)
     n_samples = W.total_samples(tab)
@@ -361,7 +365,8 @@ def run_native(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "integrands": len(tab), "samples_per_step": n_samples,
                    "quads_per_lane": info["quads_per_lane"], "chunks": info["n_chunks"],
-                   "grid": info["grid"], "block": info["block"],
+                   "grid": info["family_grid"][0], "block": info["family_block"][0],
+                   "autotune": ["default", "measured", "cached"][info["tune_source"][0]],
                    "l2": "flushed between steps (256 MiB write, outside the timed events)"},
         "plain": None if plain_ms is None else {
             "value": n_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": plain_ms,
@@ -448,6 +453,7 @@ def main():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-repeats", type=int, default=10)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=100.0)
     ap.add_argument("--serving-seconds", type=float, default=10.0)

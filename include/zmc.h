@@ -96,7 +96,9 @@ typedef struct zmc_options {
     void *stream;                /* cudaStream_t for all work; NULL -> the library
                                     creates a non-blocking stream                   */
     uint32_t max_chunks_per_iter;/* serving: chunks per persistent launch; 0 -> auto */
-    uint32_t autotune;           /* 1: time launch shapes on first use and cache     */
+    uint32_t autotune;           /* 1: time launch geometries of each family kernel
+                                    on a slice of a new plan's work (or reuse the
+                                    cache); never changes results                   */
     int32_t device;              /* CUDA device ordinal                              */
     uint32_t quads_per_lane;     /* chunk = 128 * quads_per_lane samples; 0 -> 16.
                                     Results are bit-identical for a fixed value and
@@ -113,10 +115,14 @@ typedef struct zmc_plan_info {
     uint64_t n_fn;
     uint64_t n_chunks;     /* work items of the persistent launch                  */
     uint64_t n_samples;    /* total samples over all integrands                    */
-    uint32_t grid;         /* persistent launch shape                              */
-    uint32_t block;
+    uint32_t grid;         /* largest persistent grid over the family kernels      */
+    uint32_t block;        /* default threads per block                            */
     uint32_t quads_per_lane;
     uint32_t sms;
+    uint32_t family_grid[4];   /* per family kernel (harmonic, abs-linear, Gaussian, */
+    uint32_t family_block[4];  /* polynomial); block 0 = family absent             */
+    int32_t tune_source[4];    /* 0 default geometry, 1 measured by the autotuner,  */
+                               /* 2 taken from the autotune cache                   */
 } zmc_plan_info;
 
 typedef struct zmc_serving_stats {

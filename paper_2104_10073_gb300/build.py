@@ -20,7 +20,8 @@ OUT = os.path.join(PKG, "libzmc.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp", "zmc_noalloc.cu"]
+SOURCES = ["zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp", "zmc_noalloc.cu",
+           "zmc_tune.cpp"]
 HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h"]
 
 

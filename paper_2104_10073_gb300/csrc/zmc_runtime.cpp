@@ -319,14 +319,18 @@ zmc_status ensure_stage(zmc_ctx *ctx, size_t bytes) {
   return ZMC_OK;
 }
 
-unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items) {
-  const unsigned warps_per_block = ctx->shape.block / 32;
-  unsigned bps = ctx->shape.blocks_per_sm[family];
-  if (bps == 0 || bps > static_cast<unsigned>(ctx->max_blocks_per_sm[family]))
-    bps = static_cast<unsigned>(std::max(ctx->max_blocks_per_sm[family], 1));
+unsigned grid_for(const zmc_ctx *ctx, int family, unsigned block, unsigned bps, uint64_t items) {
+  const unsigned warps_per_block = block / 32;
+  const int maxb = batched_max_blocks_per_sm(family, static_cast<int>(block));
+  if (bps == 0 || bps > static_cast<unsigned>(std::max(maxb, 1)))
+    bps = static_cast<unsigned>(std::max(maxb, 1));
   const uint64_t full = static_cast<uint64_t>(ctx->sms) * bps;
   const uint64_t need = (items + warps_per_block - 1) / warps_per_block;
   return static_cast<unsigned>(std::max<uint64_t>(1, std::min(full, need)));
+}
+
+unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items) {
+  return grid_for(ctx, family, ctx->shape.block, ctx->shape.blocks_per_sm[family], items);
 }
 
 }  // namespace zmc
@@ -353,6 +357,9 @@ struct zmc_plan {
   uint64_t n_chunks = 0, n_samples = 0;
   uint64_t fam_items[4] = {0, 0, 0, 0};
   unsigned grid[4] = {0, 0, 0, 0};
+  unsigned block[4] = {256, 256, 256, 256};
+  int tune_source[4] = {0, 0, 0, 0};  // 0 default, 1 measured, 2 from the cache
+  int dominant_dim[4] = {0, 0, 0, 0};
   cudaGraphExec_t graph = nullptr;
   std::vector<void *> blocks;
 
@@ -374,6 +381,78 @@ zmc_status check_ctx(zmc_ctx *ctx) {
   if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");
+  return ZMC_OK;
+}
+
+// Autotuner: for each family kernel of the plan, the geometry (threads per
+// block, resident blocks per SM) that runs a bounded slice of the plan's own
+// items fastest, or the cached choice for the same key.  Geometry never changes
+// results; the slice's records are recomputed identically by the real launch.
+zmc_status plan_autotune(zmc_plan *plan) {
+  zmc_ctx *ctx = plan->ctx;
+  cudaStream_t str = ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ZMC_CUDA(ctx, cudaEventCreate(&e0));
+  ZMC_CUDA(ctx, cudaEventCreate(&e1));
+  zmc_status st = ZMC_OK;
+  for (int f = 0; f < 4 && st == ZMC_OK; ++f) {
+    if (plan->fam_items[f] == 0) continue;
+    const std::string key = tune_key(ctx, f, plan->dominant_dim[f]);
+    auto hit = ctx->tune_cache.find(key);
+    if (hit != ctx->tune_cache.end()) {
+      plan->block[f] = hit->second.block;
+      plan->grid[f] = grid_for(ctx, f, hit->second.block, hit->second.blocks_per_sm,
+                               plan->fam_items[f]);
+      plan->tune_source[f] = 2;
+      continue;
+    }
+    // a slice of about 32 items per resident warp at the largest geometry
+    LaunchHdr th = plan->h_hdr;
+    const uint64_t slice = std::min<uint64_t>(plan->fam_items[f],
+                                              static_cast<uint64_t>(ctx->sms) * 64 * 32);
+    for (int g = 0; g < 4; ++g) th.item_end[g] = th.item_begin[g];
+    th.item_end[f] = th.item_begin[f] + slice;
+    TuneChoice best;
+    best.ms = 1e30f;
+    for (unsigned block : {128u, 256u}) {
+      const int maxb = batched_max_blocks_per_sm(f, static_cast<int>(block));
+      for (int bps = 1; bps <= maxb && st == ZMC_OK; ++bps) {
+        const unsigned grid = grid_for(ctx, f, block, static_cast<unsigned>(bps), slice);
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaError_t e = cudaMemcpyAsync(plan->d_hdr, &th, sizeof th, cudaMemcpyHostToDevice, str);
+          if (e == cudaSuccess) e = cudaEventRecord(e0, str);
+          if (e == cudaSuccess) e = launch_batched(f, plan->d_entries, plan->d_hdr, grid, block, str);
+          if (e == cudaSuccess) e = cudaEventRecord(e1, str);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.0f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) {
+            st = ctx_cuda_fail(ctx, e, "autotune");
+            break;
+          }
+          if (rep > 0) ms_best = std::min(ms_best, ms);  // rep 0 warms up
+        }
+        if (ms_best < best.ms) {
+          best.ms = ms_best;
+          best.block = block;
+          best.blocks_per_sm = static_cast<unsigned>(bps);
+        }
+      }
+    }
+    if (st != ZMC_OK) break;
+    plan->block[f] = best.block;
+    plan->grid[f] = grid_for(ctx, f, best.block, best.blocks_per_sm, plan->fam_items[f]);
+    plan->tune_source[f] = 1;
+    tune_cache_store(ctx, key, best);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ZMC_OK) return st;
+  // put the real header back (the slices overwrote it)
+  ZMC_CUDA(ctx, cudaMemcpyAsync(plan->d_hdr, &plan->h_hdr, sizeof plan->h_hdr,
+                                cudaMemcpyHostToDevice, str));
+  ZMC_CUDA(ctx, cudaStreamSynchronize(str));
   return ZMC_OK;
 }
 
@@ -461,7 +540,19 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
   h.quads_per_lane = ctx->quads_per_lane;
   for (int f = 0; f < 4; ++f) {
     plan->fam_items[f] = h.item_end[f] - h.item_begin[f];
+    plan->block[f] = ctx->shape.block;
     plan->grid[f] = family_grid(ctx, f, plan->fam_items[f]);
+  }
+  {
+    double dim_samples[4][kMaxDim + 1] = {{0}};
+    for (size_t i = 0; i < n; ++i)
+      dim_samples[desc[i].family][desc[i].dim] += static_cast<double>(desc[i].n_samples);
+    for (int f = 0; f < 4; ++f) {
+      int best = 0;
+      for (int dd = 1; dd <= kMaxDim; ++dd)
+        if (dim_samples[f][dd] > dim_samples[f][best]) best = dd;
+      plan->dominant_dim[f] = best;
+    }
   }
   std::vector<const FnDev *> merge(n);
   for (size_t i = 0; i < n; ++i) merge[i] = plan->d_fns + i;
@@ -493,6 +584,13 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
     plan->release_all();
     return ctx_cuda_fail(ctx, e, "plan upload");
   }
+  if (ctx->autotune) {
+    zmc_status ts = plan_autotune(plan.get());
+    if (ts != ZMC_OK) {
+      plan->release_all();
+      return ts;
+    }
+  }
   *out = plan.release();
   return ZMC_OK;
 }
@@ -505,7 +603,7 @@ zmc_status plan_enqueue(zmc_plan *plan, uint32_t stages) {
     for (int f = 0; f < 4; ++f) {
       if (plan->fam_items[f] == 0) continue;
       ZMC_CUDA(ctx, launch_batched(f, plan->d_entries, plan->d_hdr, plan->grid[f],
-                                   ctx->shape.block, str));
+                                   plan->block[f], str));
     }
   }
   if (stages & ZMC_STAGE_MERGE) {
@@ -662,6 +760,7 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   ctx->max_chunks_per_iter = opt.max_chunks_per_iter;
   ctx->autotune = opt.autotune != 0;
   if (opt.tune_cache_path) ctx->tune_cache_path = opt.tune_cache_path;
+  tune_cache_load(ctx.get());
   for (int f = 0; f < 4; ++f) ctx->max_blocks_per_sm[f] = batched_max_blocks_per_sm(f, 256);
   zmc_ctx *raw = ctx.release();
   if (opt.serving) {
@@ -753,6 +852,11 @@ zmc_status zmc_plan_info_get(const zmc_plan *plan, zmc_plan_info *out) {
   for (int f = 0; f < 4; ++f) g = std::max(g, plan->grid[f]);
   out->grid = g;
   out->block = plan->ctx->shape.block;
+  for (int f = 0; f < 4; ++f) {
+    out->family_grid[f] = plan->grid[f];
+    out->family_block[f] = plan->fam_items[f] ? plan->block[f] : 0;
+    out->tune_source[f] = plan->tune_source[f];
+  }
   out->quads_per_lane = plan->ctx->quads_per_lane;
   out->sms = static_cast<uint32_t>(plan->ctx->sms);
   return ZMC_OK;

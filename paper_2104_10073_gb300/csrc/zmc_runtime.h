@@ -51,6 +51,13 @@ struct LaunchShape {
   unsigned blocks_per_sm[4] = {0, 0, 0, 0};  // 0 -> occupancy maximum
 };
 
+// One autotuned geometry (zmc_tune.cpp).
+struct TuneChoice {
+  unsigned block = 256;
+  unsigned blocks_per_sm = 0;
+  float ms = 0.0f;
+};
+
 struct Job;
 
 }  // namespace zmc
@@ -72,6 +79,7 @@ struct zmc_ctx {
   std::string tune_cache_path;
   zmc::LaunchShape shape;
   int max_blocks_per_sm[4] = {0, 0, 0, 0};
+  std::map<std::string, zmc::TuneChoice> tune_cache;  // autotuner results by key
   std::atomic<bool> poisoned{false};
   std::recursive_mutex api_mu;  // serialises API calls that use the stream
 
@@ -88,6 +96,10 @@ namespace zmc {
 zmc_status ctx_cuda_fail(zmc_ctx *ctx, cudaError_t err, const char *what);
 zmc_status ensure_stage(zmc_ctx *ctx, size_t bytes);
 unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items);
+unsigned grid_for(const zmc_ctx *ctx, int family, unsigned block, unsigned bps, uint64_t items);
+std::string tune_key(const zmc_ctx *ctx, int family, int dim);
+void tune_cache_load(zmc_ctx *ctx);
+void tune_cache_store(zmc_ctx *ctx, const std::string &key, const TuneChoice &c);
 }  // namespace zmc
 
 // Serving state (zmc_serving.cpp).

@@ -47,7 +47,8 @@ class zmc_plan_info(ctypes.Structure):
     _fields_ = [("n_fn", ctypes.c_uint64), ("n_chunks", ctypes.c_uint64),
                 ("n_samples", ctypes.c_uint64), ("grid", ctypes.c_uint32),
                 ("block", ctypes.c_uint32), ("quads_per_lane", ctypes.c_uint32),
-                ("sms", ctypes.c_uint32)]
+                ("sms", ctypes.c_uint32), ("family_grid", ctypes.c_uint32 * 4),
+                ("family_block", ctypes.c_uint32 * 4), ("tune_source", ctypes.c_int32 * 4)]
 
 
 class zmc_serving_stats(ctypes.Structure):
@@ -223,7 +224,11 @@ def zmc_plan_device_results(plan: int) -> int:
 def zmc_plan_info_get(plan: int) -> dict:
     i = zmc_plan_info()
     _check(lib().zmc_plan_info_get(plan, ctypes.byref(i)), "zmc_plan_info_get")
-    return {name: getattr(i, name) for name, _ in i._fields_}
+    out = {}
+    for name, _ in i._fields_:
+        v = getattr(i, name)
+        out[name] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 def zmc_plan_destroy(plan: int) -> None:
@@ -276,7 +281,8 @@ class Context:
 
     def __init__(self, arena_bytes: int = 1 << 30, device: int = 0, stream=None,
                  serving: bool = False, quads_per_lane: int = 16, max_chunks_per_iter: int = 0,
-                 use_torch_memory: bool = True):
+                 use_torch_memory: bool = True, autotune: bool = False,
+                 tune_cache_path: str | None = None):
         import torch
 
         self.torch = torch
@@ -289,6 +295,9 @@ class Context:
         opt.serving = 1 if serving else 0
         opt.quads_per_lane = quads_per_lane
         opt.max_chunks_per_iter = max_chunks_per_iter
+        opt.autotune = 1 if autotune else 0
+        self._tune_path = tune_cache_path.encode() if tune_cache_path else None
+        opt.tune_cache_path = self._tune_path
         self.arena = None
         if use_torch_memory:
             self.arena = torch.empty(arena_bytes + 256, dtype=torch.uint8,

@@ -223,6 +223,35 @@ def test_plan_replay_is_bit_identical(zctx):
         zmc.zmc_plan_destroy(plan)
 
 
+def test_autotune_keeps_results_and_caches(zctx, tmp_path):
+    """The autotuner only picks launch geometry: results stay bit-identical, the
+    choice is written to the JSON cache and reused by a later context."""
+    import json
+
+    tab = W.mixed(300, gen_seed=5, lo_exp=4.0, hi_exp=6.0)
+    ref = zmc.zmc_integrate(zctx.handle, tab)
+    path = str(tmp_path / "tune.json")
+    infos = []
+    for _ in range(2):
+        with zmc.Context(arena_bytes=512 << 20, autotune=True, tune_cache_path=path) as c:
+            plan = zmc.zmc_plan_create(c.handle, tab)
+            try:
+                infos.append(zmc.zmc_plan_info_get(plan))
+                zmc.zmc_plan_run(plan)
+                got = zmc.zmc_plan_results(plan, len(tab))
+            finally:
+                zmc.zmc_plan_destroy(plan)
+        assert np.array_equal(got["estimate"], ref["estimate"])
+        assert np.array_equal(got["stderr"], ref["stderr"], equal_nan=True)
+    present = [b > 0 for b in infos[0]["family_block"]]
+    assert [s for s, p in zip(infos[0]["tune_source"], present) if p] == [1] * sum(present)
+    assert [s for s, p in zip(infos[1]["tune_source"], present) if p] == [2] * sum(present)
+    assert infos[0]["family_grid"] == infos[1]["family_grid"]
+    entries = json.load(open(path))["entries"]
+    assert len(entries) == sum(present)
+    assert all(e["block"] in (128, 256) and e["blocks_per_sm"] >= 1 for e in entries.values())
+
+
 def test_chunk_length_changes_only_rounding():
     tab = W.random_table(30, np.random.default_rng(4), n_lo=100, n_hi=40000)
     want, _ = oracle.integrate(tab)
