@@ -396,40 +396,38 @@ def run_native(args, world, rank, local):
 
 
 def run_serving(zmc, device, rate_hz, seconds):
-    """Poisson job stream through zmc_submit/zmc_poll; per-job latency submit->result."""
+    """Poisson job stream through zmc_submit; a collector thread takes finished
+    ids from zmc_poll_any and the results from zmc_poll.  Latency = submit call
+    to results collected."""
     jobs = W.serving_stream(rate_hz, seconds, max_fns=1000)
     ctx = zmc.Context(arena_bytes=8 << 30, device=device, serving=True)
+    submitted = {}
     done = {}
     lock = threading.Lock()
-    pending = []
+    n_total = len(jobs)
 
-    def poller():
-        while True:
-            with lock:
-                if not pending and stop[0]:
-                    return
-                items = list(pending)
-            for jid, n, ts in items:
-                st, _ = zmc.zmc_poll(ctx.handle, jid, n, wait_ms=0)
-                if st == zmc.ZMC_OK:
+    def collector():
+        while len(done) < n_total:
+            st, ids = zmc.zmc_poll_any(ctx.handle, 4096, 200)
+            for jid in ids:
+                with lock:
+                    ts, n = submitted[jid]
+                st2, _ = zmc.zmc_poll(ctx.handle, jid, n, wait_ms=0)
+                if st2 == zmc.ZMC_OK:
                     done[jid] = time.perf_counter() - ts
-                    with lock:
-                        pending.remove((jid, n, ts))
-            time.sleep(0.0005)
 
-    stop = [False]
-    th = threading.Thread(target=poller, daemon=True)
+    th = threading.Thread(target=collector, daemon=True)
     th.start()
     t0 = time.perf_counter()
     samples = 0
     for at, tab in jobs:
         while time.perf_counter() - t0 < at:
             time.sleep(0.0002)
-        jid = zmc.zmc_submit(ctx.handle, tab)
-        samples += W.total_samples(tab)
+        ts = time.perf_counter()
         with lock:
-            pending.append((jid, len(tab), time.perf_counter()))
-    stop[0] = True
+            jid = zmc.zmc_submit(ctx.handle, tab)
+            submitted[jid] = (ts, len(tab))
+        samples += W.total_samples(tab)
     th.join()
     wall = time.perf_counter() - t0
     ctx.close()
@@ -440,6 +438,24 @@ def run_serving(zmc, device, rate_hz, seconds):
             "p50_ms": 1e3 * lat[len(lat) // 2],
             "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "samples_per_s": samples / wall / 1e9, "unit": "Gsamples/s"}
+
+
+def run_serving_sweep(args):
+    """p50/p99 job latency and throughput over a sweep of Poisson arrival rates
+    (rank 0, one GPU); one JSON object on stdout."""
+    from paper_2104_10073_gb300 import build
+    from paper_2104_10073_gb300 import zmc
+
+    build.build()
+    out = []
+    for rate in args.serving_rates:
+        r = run_serving(zmc, 0, rate, args.serving_seconds)
+        if r is not None:
+            r["demand_gsps"] = rate * 500.5 * 1.444e6 / 1e9  # E[jobs/s x rows x N]
+        out.append(r)
+        print(json.dumps({"serving_point": r}), file=sys.stderr, flush=True)
+    print(json.dumps({"serving_sweep": out, "seconds_per_rate": args.serving_seconds,
+                      "job": "U{1..1000} mixed-style integrands, N ~ 10^U[4,7]"}), flush=True)
 
 
 def main():
@@ -454,6 +470,9 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-repeats", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serving-sweep", action="store_true")
+    ap.add_argument("--serving-rates", type=float, nargs="+",
+                    default=[10.0, 30.0, 100.0, 300.0, 1000.0])
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=100.0)
     ap.add_argument("--serving-seconds", type=float, default=10.0)
@@ -463,6 +482,9 @@ def main():
                           int(os.environ.get("LOCAL_RANK", "0")))
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.serving_sweep:
+        run_serving_sweep(args)
         return
     world, rank, local = dist_setup()
     run_native(args, world, rank, local)

@@ -177,6 +177,13 @@ zmc_status zmc_poll(zmc_ctx *ctx, uint64_t job_id, zmc_result *out, int32_t wait
 /* Cancel a queued or running job; a later poll returns ZMC_ECLOSED. */
 zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id);
 
+/* Ids of jobs that finished (done, failed or cancelled) since the last call, up
+ * to cap of them, into job_ids (host array); *n_out is the count.  Each finished
+ * job is reported once; collect its results with zmc_poll.  wait_ms as in
+ * zmc_poll (ZMC_EAGAIN / ZMC_ETIMEOUT when none finished). */
+zmc_status zmc_poll_any(zmc_ctx *ctx, uint64_t *job_ids, size_t cap, int32_t wait_ms,
+                        size_t *n_out);
+
 zmc_status zmc_serving_stats_get(zmc_ctx *ctx, zmc_serving_stats *out);
 
 /* Device-resident plan: the descriptor table precomputed and uploaded once,

@@ -95,6 +95,7 @@ struct ServingState {
   zmc_serving_stats stats{};
   zmc_status thread_status = ZMC_OK;
   uint64_t fault_at = 0;  // host-side fault injection (tests): iteration that fails
+  std::deque<uint64_t> finished;  // finished, not yet reported by zmc_poll_any
 };
 
 namespace {
@@ -183,6 +184,7 @@ void retire_slot(ServingState *S, Slot &sl) {
       j->t_done = now;
       S->stats.completed++;
       S->stats.samples_done += j->samples;
+      S->finished.push_back(j->id);
     }
     free_job_device(S, *j);
   }
@@ -221,9 +223,11 @@ void scheduler_loop(ServingState *S) {
     if (S->thread_status != ZMC_OK) {
       // fail everything that is still pending
       for (auto &kv : S->jobs)
-        if (kv.second->state != JobState::kDone && kv.second->state != JobState::kCancelled) {
+        if (kv.second->state != JobState::kDone && kv.second->state != JobState::kCancelled &&
+            kv.second->state != JobState::kFailed) {
           kv.second->state = JobState::kFailed;
           kv.second->fail_status = S->thread_status;
+          S->finished.push_back(kv.first);
         }
       S->cv_done.notify_all();
       if (S->stop) return;
@@ -285,8 +289,12 @@ void scheduler_loop(ServingState *S) {
     for (auto &j : S->live)
       if (j->state == JobState::kRunning && j->chunks_issued < j->chunks_total) active.push_back(j);
     uint32_t n_entries = 0;
+    // Each job with work left gets budget / active chunks, but at least
+    // kMinQuantum: with many live jobs, runs of a few chunks would turn every work
+    // item into an entry-table search.  Jobs are visited oldest first.
+    constexpr uint64_t kMinQuantum = 256;
     while (budget > 0 && !active.empty() && n_entries < S->max_entries) {
-      const uint64_t share = std::max<uint64_t>(1, budget / active.size());
+      const uint64_t share = std::max<uint64_t>(kMinQuantum, budget / active.size());
       std::vector<std::shared_ptr<ServJob>> still;
       for (auto &j : active) {
         uint64_t take = std::min<uint64_t>(share, budget);
@@ -551,8 +559,37 @@ zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id) {
     S->live.erase(std::remove(S->live.begin(), S->live.end(), j), S->live.end());
   }
   S->stats.cancelled++;
+  S->finished.push_back(job_id);
   S->cv_done.notify_all();
   return ZMC_OK;
+}
+
+zmc_status zmc_poll_any(zmc_ctx *ctx, uint64_t *job_ids, size_t cap, int32_t wait_ms,
+                        size_t *n_out) {
+  if (!ctx || !ctx->srv || !job_ids || !n_out || cap == 0)
+    return set_error(ZMC_EINVAL, "bad zmc_poll_any arguments");
+  ServingState *S = ctx->srv;
+  std::unique_lock<std::mutex> lk(S->mu);
+  *n_out = 0;
+  auto ready = [&] { return !S->finished.empty() || S->stop; };
+  if (!ready()) {
+    if (wait_ms == 0) return set_error(ZMC_EAGAIN, "no finished job");
+    if (wait_ms < 0) {
+      S->cv_done.wait(lk, ready);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), ready)) {
+      return set_error(ZMC_ETIMEOUT, "no job finished within %d ms", wait_ms);
+    }
+  }
+  size_t n = 0;
+  while (n < cap && !S->finished.empty()) {
+    const uint64_t id = S->finished.front();
+    S->finished.pop_front();
+    if (S->jobs.count(id)) job_ids[n++] = id;  // skip jobs already collected by zmc_poll
+  }
+  *n_out = n;
+  if (n) return ZMC_OK;
+  if (S->stop) return set_error(ZMC_ECLOSED, "context is shutting down");
+  return set_error(ZMC_EAGAIN, "no finished job");
 }
 
 zmc_status zmc_serving_stats_get(zmc_ctx *ctx, zmc_serving_stats *out) {

@@ -74,6 +74,8 @@ _SIGS = {
     "zmc_submit": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "zmc_poll": ([_P, ctypes.c_uint64, _P, ctypes.c_int32], ctypes.c_int),
     "zmc_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "zmc_poll_any": ([_P, _P, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)],
+                     ctypes.c_int),
     "zmc_serving_stats_get": ([_P, ctypes.POINTER(zmc_serving_stats)], ctypes.c_int),
     "zmc_plan_create": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)], ctypes.c_int),
     "zmc_plan_run": ([_P, ctypes.c_uint32], ctypes.c_int),
@@ -181,6 +183,14 @@ def zmc_poll(ctx: int, job_id: int, n: int, wait_ms: int = -1):
     if st == ZMC_OK:
         return st, out
     return st, None
+
+
+def zmc_poll_any(ctx: int, cap: int = 1024, wait_ms: int = -1):
+    """(status, list of finished job ids); each finished job is reported once."""
+    ids = np.zeros(cap, dtype=np.uint64)
+    n = ctypes.c_size_t(0)
+    st = lib().zmc_poll_any(ctx, ids.ctypes.data, cap, wait_ms, ctypes.byref(n))
+    return st, [int(v) for v in ids[:n.value]]
 
 
 def zmc_cancel(ctx: int, job_id: int) -> None:

@@ -157,3 +157,19 @@ def test_injected_iteration_failure_poisons_context(monkeypatch):
         got = zmc.zmc_integrate(ok.handle, t)
     want, _ = oracle.integrate(t)
     G.compare(t, got, want)
+
+
+def test_poll_any_reports_each_finished_job_once(sctx):
+    jobs = _jobs(8, seed=21, max_fns=10, hi_exp=4.5)
+    ids = {zmc.zmc_submit(sctx.handle, t): len(t) for t in jobs}
+    seen = []
+    while len(seen) < len(ids):
+        st, got = zmc.zmc_poll_any(sctx.handle, 3, 30000)
+        assert st in (zmc.ZMC_OK, zmc.ZMC_EAGAIN) and len(got) <= 3
+        seen += got
+    assert sorted(seen) == sorted(ids)
+    for jid, n in ids.items():
+        st, res = zmc.zmc_poll(sctx.handle, jid, n, wait_ms=0)
+        assert st == zmc.ZMC_OK and res is not None
+    st, got = zmc.zmc_poll_any(sctx.handle, 4, 0)
+    assert st == zmc.ZMC_EAGAIN and got == []
