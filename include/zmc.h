@@ -88,6 +88,16 @@ typedef struct zmc_result {
     int32_t reserved;
 } zmc_result;
 
+/* Moments of f over a sample range: n samples, their mean and
+ * M2 = sum (f - mean)^2 (not multiplied by the volume).  status as in zmc_result. */
+typedef struct zmc_moments {
+    double mean;
+    double m2;
+    uint64_t n;
+    int32_t status;
+    int32_t reserved;
+} zmc_moments;
+
 typedef struct zmc_options {
     uint64_t mem_budget_bytes;   /* device arena; 0 -> 1 GiB                          */
     void *arena;                 /* optional caller-owned DEVICE buffer of
@@ -159,6 +169,20 @@ zmc_status zmc_integrate(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_resul
  * merge launch.  The baseline the batched form is measured against. */
 zmc_status zmc_integrate_plain(zmc_ctx *ctx, const zmc_desc *desc, size_t n,
                                zmc_result *out);
+
+/* Moments of desc[i]'s integrand over samples [s_begin[i], s_end[i]) of its
+ * stream (host arrays; s_begin a multiple of 4, s_begin < s_end; desc[i].n_samples
+ * is ignored).  Because every sample is addressed by its Philox counter, pieces
+ * of one stream combine exactly: for pieces a, b with d = mean_b - mean_a,
+ *     n = n_a + n_b,  mean = mean_a + d n_b / n,  M2 = M2_a + M2_b + d^2 n_a n_b / n
+ * (Chan et al.), and estimate = V mean, stderr = V sqrt(M2 / (n (n-1))) of the
+ * merged moments give zmc_integrate's result for the union of the pieces (equal up
+ * to FP64 rounding; chunk-aligned boundaries, multiples of 128 * quads_per_lane,
+ * reproduce the same FP32 chunk sums).  This is how one stream is split over
+ * GPUs or processes, checkpointed between pieces, or extended to more samples
+ * later.  Blocking, like zmc_integrate. */
+zmc_status zmc_integrate_moments(zmc_ctx *ctx, const zmc_desc *desc, const uint64_t *s_begin,
+                                 const uint64_t *s_end, size_t n, zmc_moments *out);
 
 /* Serving (continuous batching).  zmc_submit copies the n descriptors into a
  * job and returns its id at once; the scheduler admits queued jobs as device

@@ -65,8 +65,11 @@ struct alignas(16) FnDev {
   zmc_result *out;    // result row written by the merge kernel
   double volume;      // prod (hi_i - lo_i), FP64
   double inv_scale;   // 1 / S (a power of two)
-  uint32_t pad[2];
-  uint32_t w[80];
+  uint64_t s_off;     // absolute index of sample 0 (a multiple of 4): sample s of
+                      // this descriptor is sample s_off + s of the Philox stream
+  uint32_t w[78];
+  uint32_t out_mode;  // merge output: 0 zmc_result (estimate, stderr), 1 zmc_moments
+  uint32_t reserved;
 };
 static_assert(sizeof(FnDev) == 384, "FnDev layout");
 

@@ -352,7 +352,7 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
   const uint64_t s0 = chunk * chunk_samples;
   const uint64_t n_left = fn->n_samples - s0;
   const uint32_t nc = static_cast<uint32_t>(n_left < chunk_samples ? n_left : chunk_samples);
-  const uint64_t quad0 = s0 >> 2;
+  const uint64_t quad0 = (fn->s_off + s0) >> 2;  // s_off is a multiple of 4
   const uint64_t block0 = quad0 * D;
   const uint32_t base_lo0 = static_cast<uint32_t>(block0) + lane * D;
   const uint32_t base_hi = static_cast<uint32_t>(block0 >> 32);
@@ -417,7 +417,7 @@ __device__ __forceinline__ void run_item(const FnDev *__restrict__ fn, uint64_t 
   const uint64_t chunk_samples = 128ull * Q;
   const uint64_t s0 = chunk * chunk_samples;
   const bool full = fn->n_samples - s0 >= chunk_samples;
-  const uint64_t b_first = (s0 >> 2) * D;
+  const uint64_t b_first = ((fn->s_off + s0) >> 2) * D;
   const uint64_t b_last = b_first + (chunk_samples >> 2) * D - 1;
   if (full && (b_first >> 32) == (b_last >> 32))
     run_chunk<FAM, D, G, true>(fn, chunk, Q, lane);
@@ -570,8 +570,13 @@ __global__ void __launch_bounds__(256) zmc_merge_kernel(const FnDev *const *__re
     if (lane == 0) {
       const double nd = static_cast<double>(N);
       zmc_result res;
-      res.estimate = fn->volume * (mean * inv);
-      res.stderr_ = fn->volume * sqrt(m2 / (nd * (nd - 1.0)));
+      if (fn->out_mode == 0) {
+        res.estimate = fn->volume * (mean * inv);
+        res.stderr_ = fn->volume * sqrt(m2 / (nd * (nd - 1.0)));
+      } else {  // zmc_moments: unscaled mean and M2 of f over the samples
+        res.estimate = mean * inv;
+        res.stderr_ = m2;
+      }
       res.n = N;
       res.status = ZMC_OK;
       res.reserved = 0;

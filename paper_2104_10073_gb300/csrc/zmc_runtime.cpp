@@ -356,6 +356,7 @@ struct zmc_plan {
   LaunchHdr h_hdr{};
   uint64_t n_chunks = 0, n_samples = 0;
   uint64_t fam_items[4] = {0, 0, 0, 0};
+  bool ranged = false;  // built by zmc_integrate_moments (no plain form)
   unsigned grid[4] = {0, 0, 0, 0};
   unsigned block[4] = {256, 256, 256, 256};
   int tune_source[4] = {0, 0, 0, 0};  // 0 default, 1 measured, 2 from the cache
@@ -456,28 +457,44 @@ zmc_status plan_autotune(zmc_plan *plan) {
   return ZMC_OK;
 }
 
-zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out) {
+// ranges: optional [s_begin[i], s_end[i]) sample ranges (moments output).
+zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out,
+                      const uint64_t *s_begin = nullptr, const uint64_t *s_end = nullptr) {
   if (!desc || !out || n == 0) return set_error(ZMC_EINVAL, "need n >= 1 descriptors");
   if (n >= (1u << 31)) return set_error(ZMC_EINVAL, "too many descriptors");
   auto plan = std::make_unique<zmc_plan>();
   plan->ctx = ctx;
   plan->n = n;
+  plan->ranged = s_begin != nullptr;
   std::vector<FnDev> fns(n);
+  std::vector<uint64_t> len(n);
   plan->plain.resize(n);
   plan->volume.resize(n);
   for (size_t i = 0; i < n; ++i) {
     zmc_status st = precompute(desc[i], &fns[i], &plan->plain[i], &plan->volume[i]);
     if (st != ZMC_OK)
       return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    len[i] = desc[i].n_samples;
+    if (s_begin) {
+      if (s_begin[i] % 4 != 0 || !(s_end[i] > s_begin[i]) || s_end[i] - s_begin[i] > (1ull << 62))
+        return set_error(ZMC_EINVAL,
+                         "range %zu: need s_begin a multiple of 4 and s_begin < s_end", i);
+      if (s_end[i] > ~0ull / kMaxDim)
+        return set_error(ZMC_EINVAL, "range %zu: sample index too large", i);
+      fns[i].s_off = s_begin[i];
+      len[i] = s_end[i] - s_begin[i];
+      fns[i].n_samples = len[i];
+      fns[i].out_mode = 1;
+    }
   }
   const uint64_t chunk = 128ull * ctx->quads_per_lane;
   std::vector<uint64_t> nchunk(n), rec_off(n);
   uint64_t total = 0, samples = 0;
   for (size_t i = 0; i < n; ++i) {
-    nchunk[i] = (desc[i].n_samples + chunk - 1) / chunk;
+    nchunk[i] = (len[i] + chunk - 1) / chunk;
     rec_off[i] = total;
     total += nchunk[i];
-    samples += desc[i].n_samples;
+    samples += len[i];
   }
   plan->n_chunks = total;
   plan->n_samples = samples;
@@ -546,7 +563,7 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
   {
     double dim_samples[4][kMaxDim + 1] = {{0}};
     for (size_t i = 0; i < n; ++i)
-      dim_samples[desc[i].family][desc[i].dim] += static_cast<double>(desc[i].n_samples);
+      dim_samples[desc[i].family][desc[i].dim] += static_cast<double>(len[i]);
     for (int f = 0; f < 4; ++f) {
       int best = 0;
       for (int dd = 1; dd <= kMaxDim; ++dd)
@@ -670,6 +687,7 @@ zmc_status plain_prepare(zmc_plan *plan) {
 
 zmc_status plain_enqueue(zmc_plan *plan) {
   zmc_ctx *ctx = plan->ctx;
+  if (plan->ranged) return set_error(ZMC_EINVAL, "the plain form runs whole descriptors only");
   zmc_status st = plain_prepare(plan);
   if (st != ZMC_OK) return st;
   for (size_t i = 0; i < plan->n; ++i)
@@ -894,6 +912,22 @@ zmc_status zmc_integrate_plain(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc
   if (st != ZMC_OK) return st;
   st = plain_enqueue(plan);
   if (st == ZMC_OK) st = plan_results_to(plan, out);
+  plan_free(plan);
+  return st;
+}
+
+zmc_status zmc_integrate_moments(zmc_ctx *ctx, const zmc_desc *desc, const uint64_t *s_begin,
+                                 const uint64_t *s_end, size_t n, zmc_moments *out) {
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  if (!out || !s_begin || !s_end) return set_error(ZMC_EINVAL, "null argument");
+  static_assert(sizeof(zmc_moments) == sizeof(zmc_result), "moments share the result slot");
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  zmc_plan *plan = nullptr;
+  st = plan_build(ctx, desc, n, &plan, s_begin, s_end);
+  if (st != ZMC_OK) return st;
+  st = plan_enqueue(plan, ZMC_STAGE_ALL);
+  if (st == ZMC_OK) st = plan_results_to(plan, reinterpret_cast<zmc_result *>(out));
   plan_free(plan);
   return st;
 }

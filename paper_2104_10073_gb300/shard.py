@@ -37,11 +37,16 @@ def partition_rows(table, world: int) -> list[np.ndarray]:
     return [np.array(sorted(r), dtype=np.int64) for r in rows]
 
 
-def partition_samples(table, world: int) -> list[list[tuple[int, int, int]]]:
-    """Contiguous (row, s_begin, s_end) pieces per rank covering every sample once."""
+def partition_samples(table, world: int, align: int = 1) -> list[list[tuple[int, int, int]]]:
+    """Contiguous (row, s_begin, s_end) pieces per rank covering every sample once.
+
+    Rank boundaries are rounded down to multiples of ``align`` within the global
+    sample sequence; ``align`` = the library's chunk length (128 * quads_per_lane)
+    makes each piece start on a chunk of its row whenever rows start on one
+    (pieces then reproduce the unsplit chunk sums exactly)."""
     n = [int(v) for v in table["n_samples"]]
     total = sum(n)
-    bounds = [total * r // world for r in range(world + 1)]
+    bounds = [(total * r // world) // align * align for r in range(world)] + [total]
     pieces = [[] for _ in range(world)]
     start = 0
     for row, cnt in enumerate(n):
@@ -80,3 +85,17 @@ def merge_moments(n_rows: int, pieces, volumes) -> np.ndarray:
         out["stderr"][i] = v * math.sqrt(m2 / (n * (n - 1))) if n > 1 else math.nan
         out["n"][i] = int(n)
     return out
+
+
+def rank_moments(ctx_handle: int, table, pieces) -> list[tuple[int, float, float, float]]:
+    """(row, n, mean, M2) of this rank's pieces computed by the library (the
+    device counterpart of the CPU oracle's moments); piece starts must be
+    multiples of 4."""
+    from . import zmc
+
+    if not pieces:
+        return []
+    rows = np.array([p[0] for p in pieces], dtype=np.int64)
+    m = zmc.zmc_integrate_moments(ctx_handle, table[rows], [p[1] for p in pieces],
+                                  [p[2] for p in pieces])
+    return [(int(r), float(k["n"]), float(k["mean"]), float(k["m2"])) for r, k in zip(rows, m)]

@@ -33,6 +33,8 @@ ZMC_STAGE_SAMPLE, ZMC_STAGE_MERGE, ZMC_STAGE_ALL = 1, 2, 3
 RESULT_DTYPE = np.dtype([("estimate", "<f8"), ("stderr", "<f8"), ("n", "<u8"),
                          ("status", "<i4"), ("reserved", "<i4")])
 assert RESULT_DTYPE.itemsize == 32
+MOMENTS_DTYPE = np.dtype([("mean", "<f8"), ("m2", "<f8"), ("n", "<u8"), ("status", "<i4"),
+                          ("reserved", "<i4")])
 
 
 class zmc_options(ctypes.Structure):
@@ -71,6 +73,7 @@ _SIGS = {
     "zmc_last_error": ([_P], ctypes.c_char_p),
     "zmc_integrate": ([_P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "zmc_integrate_plain": ([_P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "zmc_integrate_moments": ([_P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "zmc_submit": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "zmc_poll": ([_P, ctypes.c_uint64, _P, ctypes.c_int32], ctypes.c_int),
     "zmc_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
@@ -164,6 +167,18 @@ def zmc_integrate_plain(ctx: int, desc) -> np.ndarray:
     out = np.zeros(len(t), dtype=RESULT_DTYPE)
     _check(lib().zmc_integrate_plain(ctx, t.ctypes.data, len(t), out.ctypes.data),
            "zmc_integrate_plain")
+    return out
+
+
+def zmc_integrate_moments(ctx: int, desc, s_begin, s_end) -> np.ndarray:
+    """(mean, m2, n) of each row over its sample range [s_begin, s_end)."""
+    t = _table(desc)
+    b = np.ascontiguousarray(np.asarray(s_begin, dtype=np.uint64).reshape(-1))
+    e = np.ascontiguousarray(np.asarray(s_end, dtype=np.uint64).reshape(-1))
+    assert len(b) == len(e) == len(t)
+    out = np.zeros(len(t), dtype=MOMENTS_DTYPE)
+    _check(lib().zmc_integrate_moments(ctx, t.ctypes.data, b.ctypes.data, e.ctypes.data, len(t),
+                                       out.ctypes.data), "zmc_integrate_moments")
     return out
 
 

@@ -304,16 +304,41 @@ def test_invalid_descriptor_is_rejected(zctx):
 
 
 # ------------------------------------------------------------------ full size
-def test_mixed_1e4_full_size_sampled_rows(zctx):
-    """The 10^4-integrand mix at full size, in the benchmark's plan/graph launch;
-    sampled rows recomputed by the oracle one by one."""
+def _bench_config_results(tab, tmp_path):
+    """Results of ``tab`` computed exactly as bench.py times it: autotuned
+    context, device-resident plan, sampling and merge stages launched
+    separately, then one more run as the captured graph (must agree)."""
+    with zmc.Context(arena_bytes=2 << 30, autotune=True,
+                     tune_cache_path=str(tmp_path / "tune.json")) as c:
+        plan = zmc.zmc_plan_create(c.handle, tab)
+        try:
+            zmc.zmc_plan_run(plan, zmc.ZMC_STAGE_SAMPLE)
+            zmc.zmc_plan_run(plan, zmc.ZMC_STAGE_MERGE)
+            staged = zmc.zmc_plan_results(plan, len(tab))
+            zmc.zmc_plan_run(plan)
+            graph = zmc.zmc_plan_results(plan, len(tab))
+        finally:
+            zmc.zmc_plan_destroy(plan)
+    assert np.array_equal(staged["estimate"], graph["estimate"])
+    return graph
+
+
+def test_fig1x10_full_size_bench_configuration(tmp_path):
+    """The bench workload at full size (10^9 samples) in the bench's launch
+    configuration; rows sampled across all keys recomputed by the oracle."""
+    tab = W.harmonic_fig1(10**6, seeds=range(10))
+    got = _bench_config_results(tab, tmp_path)
+    assert np.array_equal(got["n"], tab["n_samples"]) and np.all(got["status"] == 0)
+    pick = np.arange(3, 1000, 41)
+    want, _ = oracle.integrate(tab[pick])
+    G.compare(tab[pick], got[pick], want)
+
+
+def test_mixed_1e4_full_size_sampled_rows(tmp_path):
+    """The 10^4-integrand mix at full size in the bench's launch configuration;
+    sampled rows of every family recomputed by the oracle one by one."""
     tab = W.mixed(10**4)
-    plan = zmc.zmc_plan_create(zctx.handle, tab)
-    try:
-        zmc.zmc_plan_run(plan)
-        got = zmc.zmc_plan_results(plan, len(tab))
-    finally:
-        zmc.zmc_plan_destroy(plan)
+    got = _bench_config_results(tab, tmp_path)
     assert np.array_equal(got["n"], tab["n_samples"])
     assert np.all(np.isfinite(got["estimate"]))
     assert np.all(got["stderr"][tab["n_samples"] > 1] >= 0)
