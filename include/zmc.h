@@ -184,6 +184,22 @@ zmc_status zmc_integrate_plain(zmc_ctx *ctx, const zmc_desc *desc, size_t n,
 zmc_status zmc_integrate_moments(zmc_ctx *ctx, const zmc_desc *desc, const uint64_t *s_begin,
                                  const uint64_t *s_end, size_t n, zmc_moments *out);
 
+/* Functional mode: one integrand form over many parameter points (the paper's
+ * ZMCintegral_functional use case, Sec. "Solution method" and "Additional
+ * comments": middle-dimensional integrands over a large parameter space).
+ * Point q is `base` with slot slots[k] set to values[q * n_slots + k]; slot j < 40
+ * is p[j], 40 + i is lo[i], 47 + i is hi[i] (ZMC_SLOT_* below).  Point q's stream
+ * is base.stream_id + q if independent_streams is nonzero, else base.stream_id
+ * for every point (common random numbers: all points see the same sample
+ * points, so differences between points carry no noise from changing samples).
+ * Results for the n_points points go to out (host).  Blocking. */
+#define ZMC_SLOT_P(j) (j)
+#define ZMC_SLOT_LO(i) (40 + (i))
+#define ZMC_SLOT_HI(i) (47 + (i))
+zmc_status zmc_integrate_functional(zmc_ctx *ctx, const zmc_desc *base, const uint32_t *slots,
+                                    uint32_t n_slots, const double *values, size_t n_points,
+                                    uint32_t independent_streams, zmc_result *out);
+
 /* Serving (continuous batching).  zmc_submit copies the n descriptors into a
  * job and returns its id at once; the scheduler admits queued jobs as device
  * memory frees up, keeps their partial sums on the device, and gives every

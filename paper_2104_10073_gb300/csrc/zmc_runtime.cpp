@@ -932,6 +932,43 @@ zmc_status zmc_integrate_moments(zmc_ctx *ctx, const zmc_desc *desc, const uint6
   return st;
 }
 
+zmc_status zmc_integrate_functional(zmc_ctx *ctx, const zmc_desc *base, const uint32_t *slots,
+                                    uint32_t n_slots, const double *values, size_t n_points,
+                                    uint32_t independent_streams, zmc_result *out) {
+  zmc_status st = check_ctx(ctx);
+  if (st != ZMC_OK) return st;
+  if (!base || !out || (n_slots && (!slots || !values)) || n_points == 0)
+    return set_error(ZMC_EINVAL, "bad functional arguments");
+  for (uint32_t k = 0; k < n_slots; ++k)
+    if (slots[k] >= ZMC_SLOT_HI(ZMC_MAX_DIM))
+      return set_error(ZMC_EINVAL, "slot %u out of range", slots[k]);
+  if (independent_streams && static_cast<uint64_t>(base->stream_id) + n_points > (1ull << 32))
+    return set_error(ZMC_EINVAL, "stream ids would exceed 32 bits");
+  std::vector<zmc_desc> table(n_points, *base);
+  for (size_t q = 0; q < n_points; ++q) {
+    zmc_desc &d = table[q];
+    for (uint32_t k = 0; k < n_slots; ++k) {
+      const uint32_t slot = slots[k];
+      const double v = values[q * n_slots + k];
+      if (slot < ZMC_NPARAM)
+        d.p[slot] = v;
+      else if (slot < ZMC_SLOT_HI(0))
+        d.lo[slot - ZMC_SLOT_LO(0)] = v;
+      else
+        d.hi[slot - ZMC_SLOT_HI(0)] = v;
+    }
+    if (independent_streams) d.stream_id = base->stream_id + static_cast<uint32_t>(q);
+  }
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  zmc_plan *plan = nullptr;
+  st = plan_build(ctx, table.data(), n_points, &plan);
+  if (st != ZMC_OK) return st;
+  st = plan_enqueue(plan, ZMC_STAGE_ALL);
+  if (st == ZMC_OK) st = plan_results_to(plan, out);
+  plan_free(plan);
+  return st;
+}
+
 zmc_status zmc_philox4x32_10(zmc_ctx *ctx, const uint32_t *ctr, const uint32_t *key,
                              uint32_t *out, size_t n) {
   zmc_status st = check_ctx(ctx);

@@ -74,6 +74,8 @@ _SIGS = {
     "zmc_integrate": ([_P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "zmc_integrate_plain": ([_P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "zmc_integrate_moments": ([_P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "zmc_integrate_functional": ([_P, _P, _P, ctypes.c_uint32, _P, ctypes.c_size_t,
+                                  ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_submit": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "zmc_poll": ([_P, ctypes.c_uint64, _P, ctypes.c_int32], ctypes.c_int),
     "zmc_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
@@ -179,6 +181,32 @@ def zmc_integrate_moments(ctx: int, desc, s_begin, s_end) -> np.ndarray:
     out = np.zeros(len(t), dtype=MOMENTS_DTYPE)
     _check(lib().zmc_integrate_moments(ctx, t.ctypes.data, b.ctypes.data, e.ctypes.data, len(t),
                                        out.ctypes.data), "zmc_integrate_moments")
+    return out
+
+
+def slot_p(j: int) -> int:
+    return j
+
+
+def slot_lo(i: int) -> int:
+    return 40 + i
+
+
+def slot_hi(i: int) -> int:
+    return 47 + i
+
+
+def zmc_integrate_functional(ctx: int, base_row, slots, values, independent_streams=True):
+    """Results of ``base_row`` at each parameter point: row q of ``values``
+    (n_points x len(slots)) sets the given slots (see slot_p / slot_lo / slot_hi)."""
+    t = _table(np.asarray(base_row).reshape(1))
+    sl = np.ascontiguousarray(np.asarray(slots, dtype=np.uint32).reshape(-1))
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1, len(sl)))
+    out = np.zeros(v.shape[0], dtype=RESULT_DTYPE)
+    _check(lib().zmc_integrate_functional(ctx, t.ctypes.data, sl.ctypes.data, len(sl),
+                                          v.ctypes.data, v.shape[0],
+                                          1 if independent_streams else 0, out.ctypes.data),
+           "zmc_integrate_functional")
     return out
 
 
