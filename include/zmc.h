@@ -204,7 +204,8 @@ zmc_status zmc_integrate_functional(zmc_ctx *ctx, const zmc_desc *base, const ui
  * job and returns its id at once; the scheduler admits queued jobs as device
  * memory frees up, keeps their partial sums on the device, and gives every
  * persistent launch a share of the chunks of every admitted job.  A job that
- * alone exceeds the memory budget is refused with ZMC_ENOMEM.
+ * alone exceeds the memory budget is refused with ZMC_ENOMEM; a job may hold at
+ * most 43690 integrands (ZMC_EINVAL beyond).
  * Requires opt->serving = 1. */
 zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *job_id);
 

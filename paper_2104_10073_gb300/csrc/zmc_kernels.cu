@@ -334,10 +334,17 @@ __device__ __forceinline__ void warp_chan_merge(float &n, float &mean, float &m2
 // turns them into (n, mean = s1/n, M2 = s2 - n (mean - K)^2) and merges that into
 // the lane's running summary (Chan's pairwise update); the warp then merges the
 // 32 lane summaries the same way.
+// Quads of one lane interleaved per loop step, per family (build-time knobs).
 #ifndef ZMC_QUAD_UNROLL
 #define ZMC_QUAD_UNROLL 1
 #endif
-constexpr int kQuadUnroll = ZMC_QUAD_UNROLL;  // quads of one lane interleaved per step
+#ifndef ZMC_QUAD_UNROLL_HARMONIC
+#define ZMC_QUAD_UNROLL_HARMONIC ZMC_QUAD_UNROLL
+#endif
+template <int FAM>
+struct QuadUnroll {
+  static constexpr int value = FAM == ZMC_HARMONIC ? ZMC_QUAD_UNROLL_HARMONIC : ZMC_QUAD_UNROLL;
+};
 // Quads per accumulation block: a lane's shifted sums never span more than
 // 4 * kBlockQuads samples, which bounds their rounding error for any chunk length.
 constexpr uint32_t kBlockQuads = 16;
@@ -363,7 +370,7 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
     const uint32_t je = jb + kBlockQuads < Q ? jb + kBlockQuads : Q;
     float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
     uint32_t cnt = 0;
-#pragma unroll kQuadUnroll
+#pragma unroll QuadUnroll<FAM>::value
     for (uint32_t j = jb; j < je; ++j) {
       const uint32_t ql = lane + 32u * j;
       if (!FAST && 4u * ql >= nc) break;

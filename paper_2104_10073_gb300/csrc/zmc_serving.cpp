@@ -109,9 +109,12 @@ void free_job_device(ServingState *S, ServJob &j) {
   }
 }
 
-// Admission: one arena block per job; upload its descriptor table.
-bool try_admit(ServingState *S, ServJob &j) {
+// Admission: one arena block per job; its descriptor table is copied into the
+// slot's pinned admission area and uploaded asynchronously from there.
+bool try_admit(ServingState *S, ServJob &j, char *stage, size_t &stage_used, size_t stage_cap) {
   zmc_ctx *ctx = S->ctx;
+  const size_t tbytes = j.n * sizeof(FnDev);
+  if (stage_used + tbytes > stage_cap) return false;
   char *blk = static_cast<char *>(ctx->arena.alloc(j.block_bytes));
   if (!blk) return false;
   j.dblock = blk;
@@ -126,9 +129,10 @@ bool try_admit(ServingState *S, ServJob &j) {
     j.fns[i].out = j.d_out + i;
     r += j.nchunk[i];
   }
-  // pageable source: the copy completes before cudaMemcpyAsync returns
-  cudaError_t e = cudaMemcpyAsync(j.d_fns, j.fns.data(), j.n * sizeof(FnDev),
-                                  cudaMemcpyHostToDevice, S->stream);
+  char *src = stage + stage_used;
+  std::memcpy(src, j.fns.data(), tbytes);
+  stage_used += round256(tbytes);
+  cudaError_t e = cudaMemcpyAsync(j.d_fns, src, tbytes, cudaMemcpyHostToDevice, S->stream);
   if (e != cudaSuccess) {
     ctx_cuda_fail(ctx, e, "serving admission upload");
     S->thread_status = ZMC_ECUDA;
@@ -162,9 +166,16 @@ zmc_status build_slot_graph(ServingState *S, Slot &sl) {
   return ZMC_OK;
 }
 
+constexpr size_t kAdmitBytes = 16u << 20;  // pinned admission area per slot
+
 size_t stage_bytes(const ServingState *S) {
   return round256(S->max_entries * sizeof(Entry)) + round256(S->max_merge * sizeof(FnDev *)) +
-         round256(sizeof(LaunchHdr)) + round256(S->max_merge * sizeof(zmc_result));
+         round256(sizeof(LaunchHdr)) + round256(S->max_merge * sizeof(zmc_result)) +
+         kAdmitBytes;
+}
+
+char *admit_area(const ServingState *S, const Slot &sl) {
+  return sl.h_stage + stage_bytes(S) - kAdmitBytes;
 }
 
 // Retire a completed slot: results to jobs, device blocks back to the arena.
@@ -234,17 +245,6 @@ void scheduler_loop(ServingState *S) {
       S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
       continue;
     }
-    // admission in arrival order
-    while (!S->queue.empty()) {
-      auto j = S->queue.front();
-      if (j->state == JobState::kCancelled) {
-        S->queue.pop_front();
-        continue;
-      }
-      if (!try_admit(S, *j)) break;
-      S->queue.pop_front();
-      S->live.push_back(j);
-    }
     // pick a free slot
     Slot *slot = nullptr;
     for (auto &sl : S->slots)
@@ -252,6 +252,29 @@ void scheduler_loop(ServingState *S) {
         slot = &sl;
         break;
       }
+    // admission in arrival order, staged through the free slot's pinned area
+    if (slot) {
+      size_t used = 0;
+      char *area = admit_area(S, *slot);
+      while (!S->queue.empty()) {
+        auto j = S->queue.front();
+        if (j->state == JobState::kCancelled) {
+          S->queue.pop_front();
+          continue;
+        }
+        if (j->n * sizeof(FnDev) > kAdmitBytes) {  // never fits the area: refused
+          j->state = JobState::kFailed;
+          j->fail_status = ZMC_ENOMEM;
+          S->finished.push_back(j->id);
+          S->queue.pop_front();
+          S->cv_done.notify_all();
+          continue;
+        }
+        if (!try_admit(S, *j, area, used, kAdmitBytes)) break;
+        S->queue.pop_front();
+        S->live.push_back(j);
+      }
+    }
     const bool have_work = !S->live.empty() || !S->to_merge.empty();
     if (!slot || !have_work) {
       bool any_busy = S->slots[0].busy || S->slots[1].busy;
@@ -283,6 +306,7 @@ void scheduler_loop(ServingState *S) {
     LaunchHdr *hdr = reinterpret_cast<LaunchHdr *>(
         st + round256(S->max_entries * sizeof(Entry)) + round256(S->max_merge * sizeof(FnDev *)));
     std::vector<Entry> fam_ents[4];
+    std::unordered_map<const FnDev *, uint32_t> variant_of;
     uint64_t budget = S->max_chunks;
     // fair share: equal split, leftovers handed out on further passes
     std::vector<std::shared_ptr<ServJob>> active;
@@ -307,6 +331,7 @@ void scheduler_loop(ServingState *S) {
           en.fn = j->d_fns + i;
           en.chunk_begin = j->next_chunk[i];
           fam_ents[j->family[i]].push_back(en);
+          variant_of[en.fn] = j->fns[i].variant;
           // remember the run length in item_begin for now
           fam_ents[j->family[i]].back().item_begin = t;
           ++n_entries;
@@ -325,11 +350,27 @@ void scheduler_loop(ServingState *S) {
       }
       active.swap(still);
     }
-    // concatenate by family; convert run lengths into item offsets
+    // concatenate by family, each family's runs ordered by variant (stable) so
+    // co-resident warps mostly run the same code path, as in a plan;
+    // convert run lengths into item offsets
     std::memset(hdr, 0, sizeof *hdr);
     uint64_t item = 0;
     uint32_t k = 0;
     for (int f = 0; f < 4; ++f) {
+      auto &fe = fam_ents[f];
+      std::vector<uint32_t> var(fe.size());
+      for (size_t q = 0; q < fe.size(); ++q) {
+        const FnDev *dev = fe[q].fn;
+        // the host copy of the descriptor holds the variant; find it by job
+        var[q] = variant_of.at(dev);
+      }
+      std::vector<uint32_t> order(fe.size());
+      for (size_t q = 0; q < order.size(); ++q) order[q] = static_cast<uint32_t>(q);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](uint32_t a, uint32_t b) { return var[a] < var[b]; });
+      std::vector<Entry> sorted(fe.size());
+      for (size_t q = 0; q < order.size(); ++q) sorted[q] = fe[order[q]];
+      fe.swap(sorted);
       hdr->item_begin[f] = item;
       for (auto &en : fam_ents[f]) {
         const uint64_t len = en.item_begin;
@@ -496,8 +537,8 @@ zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *jo
   }
   j->block_bytes = round256(n * sizeof(FnDev)) + round256(j->chunks_total * sizeof(float2)) +
                    round256(n * sizeof(zmc_result));
-  if (n > S->max_merge)
-    return set_error(ZMC_EINVAL, "a job may hold at most %u integrands", S->max_merge);
+  const size_t max_fns = std::min<size_t>(S->max_merge, kAdmitBytes / sizeof(FnDev));
+  if (n > max_fns) return set_error(ZMC_EINVAL, "a job may hold at most %zu integrands", max_fns);
   if (j->block_bytes > ctx->arena.size())
     return set_error(ZMC_ENOMEM, "job needs %zu bytes; the arena has %zu", j->block_bytes,
                      ctx->arena.size());
