@@ -39,17 +39,20 @@ UNIT = "Gsamples/s"
 WORKLOAD = "fig1-harmonics-100x1e6-x10-repeats"
 
 # Algorithmic 32-bit operations per sample of a d-dimensional harmonic (the
-# dominant kernel of the default workload), counted from the method's minimal
-# steps: Philox4x32-10 = 10 rounds x (2 widening multiplies + 2 three-way XORs)
-# per 4 words -> 10 d; per coordinate: 23-bit mask + 64-bit fixed-point
-# multiply-add (2) -> 3 d; phase fraction, quadrant and remainder -> 6;
-# sin and cos polynomials -> 10; quadrant rotation and a cos + b sin -> 8;
-# shifted sums -> 3.
+# dominant kernel of the default workload), counted from the minimal steps of
+# the kernel's method: Philox4x32-10 = 10 rounds x (2 widening multiplies + 2
+# three-way XORs) per 4 words -> 10 d; per coordinate: 23-bit mask, the high-word
+# phase multiply-add, the low-word FMA and the add of its bits -> 4 d; the phase
+# carry, |x|, 1/4 - |x|, the integer -> float conversion and its scaling -> 5;
+# t^2, the degree-5 odd polynomial (5) and the amplitude (2) -> 8; shifted
+# sums -> 3.
 def harmonic_ops_per_sample(d: int) -> int:
-    return 10 * d + 3 * d + 6 + 10 + 8 + 3
+    return 10 * d + 4 * d + 5 + 8 + 3
 
 
-KERNEL_SOURCES = ["paper_2104_10073_gb300/csrc/zmc_kernels.cu",
+# Sources of the dominant kernel (zmc_batched_kernel<HARMONIC>).
+KERNEL_SOURCES = ["paper_2104_10073_gb300/csrc/zmc_fam_harmonic.cu",
+                  "paper_2104_10073_gb300/csrc/zmc_device.cuh",
                   "paper_2104_10073_gb300/csrc/zmc_internal.h",
                   "paper_2104_10073_gb300/csrc/zmc_coeffs.h"]
 PROFILE = os.path.join(ROOT, "profiles", "zmc_batched_harmonic_fig1x10.md")
@@ -329,20 +332,27 @@ def run_native(args, world, rank, local):
         zmc.zmc_plan_run(mp)
         ctx.stream.synchronize()
         st, _ = time_plan(zmc, torch, ctx, mp, 3, flush)
-        zmc.zmc_plan_run_plain(mp)
-        ctx.stream.synchronize()
-        e0.record(ctx.stream)
-        zmc.zmc_plan_run_plain(mp)
-        e1.record(ctx.stream)
-        ctx.stream.synchronize()
-        pms = e0.elapsed_time(e1)
         ns = W.total_samples(mt)
         mixed = {"workload": "mixed-1e4-integrands-d1..7-logN4..7", "samples": ns,
                  "batched_gsps": ns / (statistics.median(st) / 1e3) / 1e9,
-                 "plain_gsps": ns / (pms / 1e3) / 1e9,
-                 "batched_ms": statistics.median(st), "plain_ms": pms}
-        mixed["batched_over_plain"] = mixed["batched_gsps"] / mixed["plain_gsps"]
+                 "batched_ms": statistics.median(st)}
+        if not args.skip_plain:
+            zmc.zmc_plan_run_plain(mp)
+            ctx.stream.synchronize()
+            e0.record(ctx.stream)
+            zmc.zmc_plan_run_plain(mp)
+            e1.record(ctx.stream)
+            ctx.stream.synchronize()
+            pms = e0.elapsed_time(e1)
+            mixed["plain_gsps"] = ns / (pms / 1e3) / 1e9
+            mixed["plain_ms"] = pms
+            mixed["batched_over_plain"] = mixed["batched_gsps"] / mixed["plain_gsps"]
         zmc.zmc_plan_destroy(mp)
+
+    functional = checkpoint = None
+    if rank == 0 and not args.skip_modes:
+        functional = run_functional(zmc, ctx)
+        checkpoint = run_checkpoint(zmc, local, ctx)
 
     serving = None
     if rank == 0 and not args.skip_serving:
@@ -373,6 +383,8 @@ def run_native(args, world, rank, local):
             "dtype": "f64", "form": "one FP64 kernel launch per integrand + merge"},
         "batched_over_plain": None if plain_ms is None else plain_ms / (sum(step_ms) / len(step_ms)),
         "mixed": mixed,
+        "functional": functional,
+        "checkpoint": checkpoint,
         "serving": serving,
         "e2e": None if e2e_s is None else {
             "value": total / e2e_s / 1e9, "unit": UNIT,
@@ -440,6 +452,65 @@ def run_serving(zmc, device, rate_hz, seconds):
             "samples_per_s": samples / wall / 1e9, "unit": "Gsamples/s"}
 
 
+def run_functional(zmc, ctx):
+    """Functional mode: one 4-D harmonic over a 1000-point lattice of its wave
+    vector (k_1 = k_2 = k_3 = k_4 = kappa, kappa from 8.1 to 23.9, the Fig. 1
+    range), 10^6 samples per point, common random numbers; end to end through
+    zmc_integrate_functional (lattice in from the host, results out)."""
+    base = W.harmonic_fig1(10**6)[0]
+    kappa = np.linspace(51.0 / (2 * np.pi), 150.0 / (2 * np.pi), 1000)
+    values = np.repeat(kappa[:, None], 4, axis=1)
+    slots = [zmc.slot_p(2 + i) for i in range(4)]
+    zmc.zmc_integrate_functional(ctx.handle, base, slots, values, False)
+    t = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        out = zmc.zmc_integrate_functional(ctx.handle, base, slots, values, False)
+        t.append(time.perf_counter() - t0)
+    assert np.all(out["status"] == 0)
+    sec = statistics.median(t)
+    n = len(values) * 10**6
+    return {"workload": "harmonic-4d-1000-kappa-points-x1e6-common-streams", "samples": n,
+            "value": n / sec / 1e9, "unit": UNIT, "ms": 1e3 * sec,
+            "path": "zmc_integrate_functional (host lattice in, host results out)"}
+
+
+def run_checkpoint(zmc, device, ref_ctx):
+    """Preemption of a serving job: 1000 Fig. 1 harmonics x 10^7 samples
+    (10^10 samples) submitted, checkpointed after ~10 ms, resumed; reports the
+    checkpoint call's latency, the time of the interrupted + resumed run against
+    an uninterrupted one, and the largest difference of the final estimates from
+    the uninterrupted run in units of their standard error."""
+    tab = W.harmonic_fig1(10**7, seeds=range(10))
+    ctx = zmc.Context(arena_bytes=2 << 30, device=device, serving=True)
+    jid = zmc.zmc_submit(ctx.handle, tab)  # warm-up: graphs, pinned areas
+    zmc.zmc_poll(ctx.handle, jid, len(tab), wait_ms=-1)
+    t0 = time.perf_counter()
+    jid = zmc.zmc_submit(ctx.handle, tab)
+    st, whole = zmc.zmc_poll(ctx.handle, jid, len(tab), wait_ms=-1)
+    t_whole = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    jid = zmc.zmc_submit(ctx.handle, tab)
+    time.sleep(0.010)
+    tc = time.perf_counter()
+    st, ck = zmc.zmc_checkpoint(ctx.handle, jid, len(tab), wait_ms=-1)
+    t_ckpt = time.perf_counter() - tc
+    if st != zmc.ZMC_OK:
+        ctx.close()
+        return {"status": int(st)}
+    rid = zmc.zmc_submit_resume(ctx.handle, tab, ck)
+    st, res = zmc.zmc_poll(ctx.handle, rid, len(tab), wait_ms=-1)
+    t_both = time.perf_counter() - t0
+    ctx.close()
+    dev = np.abs(res["estimate"] - whole["estimate"]) / whole["stderr"]
+    return {"workload": "fig1-harmonics-100x1e7-x10-keys-one-job", "samples": W.total_samples(tab),
+            "checkpoint_ms": 1e3 * t_ckpt,
+            "done_at_checkpoint": float(ck["n"].sum() / W.total_samples(tab)),
+            "rows_partial_at_checkpoint": int(np.sum((ck["n"] > 0) & (ck["n"] < tab["n_samples"]))),
+            "uninterrupted_ms": 1e3 * t_whole, "checkpoint_resume_ms": 1e3 * t_both,
+            "max_abs_diff_in_stderr": float(dev.max())}
+
+
 def run_serving_sweep(args):
     """p50/p99 job latency and throughput over a sweep of Poisson arrival rates
     (rank 0, one GPU); one JSON object on stdout."""
@@ -468,7 +539,9 @@ def main():
     ap.add_argument("--skip-mixed", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
-    ap.add_argument("--cpu-repeats", type=int, default=10)
+    ap.add_argument("--skip-modes", action="store_true",
+                    help="skip the functional-mode and checkpoint/resume legs")
+    ap.add_argument("--cpu-repeats", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-sweep", action="store_true")
     ap.add_argument("--serving-rates", type=float, nargs="+",

@@ -218,6 +218,33 @@ zmc_status zmc_poll(zmc_ctx *ctx, uint64_t job_id, zmc_result *out, int32_t wait
 /* Cancel a queued or running job; a later poll returns ZMC_ECLOSED. */
 zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id);
 
+/* Checkpoint a job and release it (preemption, migration, shutdown).  The job
+ * stops receiving chunks at once; when the chunks already in flight have
+ * finished, out[i] (n entries, host) holds the moments of every sample integrand
+ * i has taken so far -- the first out[i].n samples of its stream, a multiple of
+ * 128 * quads_per_lane unless the integrand is complete -- including the moments
+ * it was resumed from.  A queued job is released at once with its starting
+ * moments (n = 0 for a fresh job).  Samples are addressed by their Philox
+ * counter (Sec. "Solution method": direct MC per integrand; the generator is
+ * counter-based), so zmc_submit_resume continues each stream exactly where the
+ * checkpoint stopped, on this or any other context.
+ * wait_ms as in zmc_poll; after ZMC_ETIMEOUT the checkpoint stays under way and
+ * a later call with the same id collects it.  A job that has already issued all
+ * of its samples is not stopped: ZMC_EAGAIN, collect it with zmc_poll.  A later
+ * zmc_poll of a checkpointed id returns ZMC_ECLOSED or ZMC_ENOTFOUND. */
+zmc_status zmc_checkpoint(zmc_ctx *ctx, uint64_t job_id, zmc_moments *out, int32_t wait_ms);
+
+/* Submit a job that continues from moments taken earlier (a zmc_checkpoint, or
+ * zmc_integrate_moments over samples [0, from[i].n) of the same stream):
+ * integrand i samples [from[i].n, desc[i].n_samples) of its stream and its
+ * result combines from[i] with them (Chan's pairwise update on the device), so
+ * that it equals an uninterrupted run of desc[i] up to FP64 rounding of the
+ * merge.  Needs from[i].n <= desc[i].n_samples and from[i].n a multiple of 4 or
+ * equal to n_samples (ZMC_EINVAL otherwise); from[i].n = 0 starts afresh.
+ * Otherwise as zmc_submit. */
+zmc_status zmc_submit_resume(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *from,
+                             size_t n, uint64_t *job_id);
+
 /* Ids of jobs that finished (done, failed or cancelled) since the last call, up
  * to cap of them, into job_ids (host array); *n_out is the count.  Each finished
  * job is reported once; collect its results with zmc_poll.  wait_ms as in

@@ -1,8 +1,10 @@
 """Build ``libzmc.so`` (the C ABI library) in-tree with nvcc for sm_103a.
 
-Three translation units compile in parallel (kernels, runtime, serving) and link
-into one shared library with the CUDA runtime linked statically, so the library
-needs only the NVIDIA driver at run time.  Output:
+The translation units (one per integrand family's sampling path, the plain form,
+the shared kernels, the host runtime, serving, the allocation-free entry point,
+the tuning cache) compile in parallel and link into one shared library with the
+CUDA runtime linked statically, so the library needs only the NVIDIA driver at
+run time.  Output:
 ``paper_2104_10073_gb300/libzmc.so``.  Rebuilds only when a source is newer.
 """
 from __future__ import annotations
@@ -20,9 +22,10 @@ OUT = os.path.join(PKG, "libzmc.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp", "zmc_noalloc.cu",
-           "zmc_tune.cpp"]
-HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h"]
+SOURCES = ["zmc_fam_harmonic.cu", "zmc_fam_abslin.cu", "zmc_fam_gauss.cu", "zmc_fam_poly.cu",
+           "zmc_plain.cu", "zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp",
+           "zmc_noalloc.cu", "zmc_tune.cpp"]
+HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h", "zmc_device.cuh"]
 
 
 def _nvcc() -> str:

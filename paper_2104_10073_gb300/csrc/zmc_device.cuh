@@ -1,0 +1,399 @@
+// zmc_device.cuh -- device code shared by the sm_103a kernels of multi-function
+// direct Monte Carlo (ZMCintegral-v5.1 multi-function mode, arXiv 2104.10073):
+// the Philox4x32-10 generator, the uniform -> box map, the per-chunk FP32
+// accumulation, and the persistent work-list kernel template.
+//
+// Each integrand family's sampling path is its own translation unit
+// (zmc_fam_<family>.cu): it specialises Eval<FAM, D, G> (the FP32 integrand) and
+// dispatch_item / dispatch_eval (variant -> specialised body), then defines its
+// FamilyOps from family_ops<FAM>().  Everything here has internal linkage, so a
+// kernel is instantiated only in the file of its family.
+#pragma once
+
+#include <cstdint>
+
+#include "zmc_internal.h"
+
+namespace zmc {
+namespace {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): round multipliers and the
+// Weyl increments of the key schedule.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Round keys hoisted once per chunk (the key is the integrand's, warp uniform).
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ RoundKeys make_round_keys(uint32_t key0, uint32_t key1) {
+  RoundKeys rk;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = key0 + static_cast<uint32_t>(r) * kPhiloxW0;
+    rk.k1[r] = key1 + static_cast<uint32_t>(r) * kPhiloxW1;
+  }
+  return rk;
+}
+
+// Ten rounds of the 4x32 S-box: two 32x32->64 products, two three-way XORs.
+// ZMC_PHILOX_MULHI selects separate high / low multiplies instead of one
+// widening multiply per product (same results; a scheduling choice).
+#ifndef ZMC_PHILOX_MULHI
+#define ZMC_PHILOX_MULHI 0
+#endif
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+#if ZMC_PHILOX_MULHI
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+#else
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+    const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+    const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+#endif
+    const uint32_t n0 = hi1 ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = hi0 ^ c3 ^ rk.k1[r];
+    c1 = lo1;
+    c3 = lo0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// The 4*D words of one quad (4 consecutive samples starting at a multiple of 4):
+// sample t, coordinate i is word t*D + i, i.e. lane (t*D+i)%4 of Philox block
+// quad*D + (t*D+i)/4.  FAST: the caller guarantees the block index's high word is
+// the same for the whole chunk, so only the low word advances.
+template <int D, bool FAST>
+__device__ __forceinline__ void gen_quad(uint64_t quad, uint32_t base_lo, uint32_t base_hi,
+                                         uint32_t sid, const RoundKeys &rk, uint32_t (&r)[4 * D]) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    uint32_t lo, hi;
+    if (FAST) {
+      lo = base_lo + static_cast<uint32_t>(j);
+      hi = base_hi;
+    } else {
+      const uint64_t b = quad * D + static_cast<uint64_t>(j);
+      lo = static_cast<uint32_t>(b);
+      hi = static_cast<uint32_t>(b >> 32);
+    }
+    const uint4 o = philox(lo, hi, sid, 0u, rk);
+    r[4 * j + 0] = o.x;
+    r[4 * j + 1] = o.y;
+    r[4 * j + 2] = o.z;
+    r[4 * j + 3] = o.w;
+  }
+}
+
+__device__ __forceinline__ float unit_v(uint32_t word) {
+  // v = 1 + (word & 0x7FFFFF) * 2^-23 in [1, 2), exact: one LOP3.
+  return __uint_as_float((word & 0x7FFFFFu) | 0x3F800000u);
+}
+
+// ---------------------------------------------------------------- integrands (FP32)
+// Eval<FAM, D, G>: load(fn) reads the integrand's FP32 constants from FnDev;
+// operator()(r) returns the scaled value f' = S f at the sample whose D Philox
+// words are r[0..D).  Specialised per family in zmc_fam_<family>.cu.
+template <int FAM, int D, int G>
+struct Eval;
+
+// ---------------------------------------------------------------- one chunk
+// Chan's pairwise merge of (n, mean, M2) summaries, FP32, down the warp; lane 0
+// ends with the warp's summary.
+__device__ __forceinline__ void warp_chan_merge(float &n, float &mean, float &m2) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const float nb = __shfl_down_sync(kFullMask, n, off);
+    const float mb = __shfl_down_sync(kFullMask, mean, off);
+    const float m2b = __shfl_down_sync(kFullMask, m2, off);
+    const float nab = n + nb;
+    if (nb > 0.0f) {
+      const float delta = mb - mean;
+      const float wb = __fdiv_rn(nb, nab);
+      mean = fmaf(delta, wb, mean);
+      m2 = m2 + m2b + delta * delta * (n * wb);
+      n = nab;
+    }
+  }
+}
+
+// FP64 butterfly sum over the warp (every lane ends with the total).
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(kFullMask, v, off);
+  return v;
+}
+
+// Samples [chunk * 128Q, min(+128Q, N)) of one integrand.  Lane l takes quads
+// l, l+32, ..., l+32(Q-1) of the chunk.  Over each block of kBlockQuads of its
+// quads it accumulates in FP32
+//   s1 = sum f            (each quad summed pairwise first; unshifted, so its
+//                          rounding error scales with the values themselves)
+//   s2 = sum (f - K)^2    (K = the block's first value, so that s2 does not hold
+//                          mean^2 n when the spread is small)
+// turns them into (n, mean = s1/n, M2 = s2 - n (mean - K)^2) and merges that into
+// the lane's running summary (Chan's pairwise update); the warp then merges the
+// 32 lane summaries the same way.
+// Quads of one lane interleaved per loop step, per family (build-time knobs).
+#ifndef ZMC_QUAD_UNROLL
+#define ZMC_QUAD_UNROLL 1
+#endif
+#ifndef ZMC_QUAD_UNROLL_HARMONIC
+#define ZMC_QUAD_UNROLL_HARMONIC ZMC_QUAD_UNROLL
+#endif
+template <int FAM>
+struct QuadUnroll {
+  static constexpr int value = FAM == ZMC_HARMONIC ? ZMC_QUAD_UNROLL_HARMONIC : ZMC_QUAD_UNROLL;
+};
+// Quads per accumulation block: a lane's shifted sums never span more than
+// 4 * kBlockQuads samples, which bounds their rounding error for any chunk length.
+constexpr uint32_t kBlockQuads = 16;
+template <int FAM, int D, int G, bool FAST>
+__device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t chunk,
+                                          uint32_t Q, uint32_t lane) {
+  Eval<FAM, D, G> ev;
+  ev.load(fn);
+  const RoundKeys rk = make_round_keys(fn->key0, fn->key1);
+  const uint32_t sid = fn->stream_id;
+  const uint64_t chunk_samples = 128ull * Q;
+  const uint64_t s0 = chunk * chunk_samples;
+  const uint64_t n_left = fn->n_samples - s0;
+  const uint32_t nc = static_cast<uint32_t>(n_left < chunk_samples ? n_left : chunk_samples);
+  const uint64_t quad0 = (fn->s_off + s0) >> 2;  // s_off is a multiple of 4
+  const uint64_t block0 = quad0 * D;
+  const uint32_t base_lo0 = static_cast<uint32_t>(block0) + lane * D;
+  const uint32_t base_hi = static_cast<uint32_t>(block0 >> 32);
+
+  // running (n, mean, M2) of the lane, merged from blocks of kBlockQuads quads
+  float n = 0.0f, mean = 0.0f, m2 = 0.0f;
+  for (uint32_t jb = 0; jb < Q; jb += kBlockQuads) {
+    const uint32_t je = jb + kBlockQuads < Q ? jb + kBlockQuads : Q;
+    float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    uint32_t cnt = 0;
+#pragma unroll QuadUnroll<FAM>::value
+    for (uint32_t j = jb; j < je; ++j) {
+      const uint32_t ql = lane + 32u * j;
+      if (!FAST && 4u * ql >= nc) break;
+      uint32_t r[4 * D];
+      gen_quad<D, FAST>(quad0 + ql, base_lo0 + 32u * D * j, base_hi, sid, rk, r);
+      float f[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) f[t] = ev(r + t * D);
+      if (j == jb) K = f[0];
+      if (FAST) {
+        s1 += (f[0] + f[1]) + (f[2] + f[3]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float dlt = f[t] - K;
+          s2 = fmaf(dlt, dlt, s2);
+        }
+      } else {
+        float q[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const bool ok = 4u * ql + t < nc;
+          q[t] = ok ? f[t] : 0.0f;
+          const float dlt = ok ? f[t] - K : 0.0f;
+          s2 = fmaf(dlt, dlt, s2);
+          cnt += ok ? 1u : 0u;
+        }
+        s1 += (q[0] + q[1]) + (q[2] + q[3]);
+      }
+    }
+    const float nb = FAST ? static_cast<float>(4u * (je - jb)) : static_cast<float>(cnt);
+    if (nb > 0.0f) {
+      const float mb = __fdiv_rn(s1, nb);
+      const float dk = mb - K;
+      const float m2b = fmaxf(fmaf(-nb * dk, dk, s2), 0.0f);
+      const float nab = n + nb;
+      const float delta = mb - mean;
+      const float wb = __fdiv_rn(nb, nab);
+      mean = fmaf(delta, wb, mean);
+      m2 = m2 + m2b + delta * delta * (n * wb);
+      n = nab;
+    }
+    if (!FAST && cnt < 4u * (je - jb)) break;
+  }
+  warp_chan_merge(n, mean, m2);
+  if (lane == 0) fn->rec[chunk] = make_float2(mean, m2);
+}
+
+template <int FAM, int D, int G>
+__device__ __forceinline__ void run_item(const FnDev *__restrict__ fn, uint64_t chunk,
+                                         uint32_t Q, uint32_t lane) {
+  const uint64_t chunk_samples = 128ull * Q;
+  const uint64_t s0 = chunk * chunk_samples;
+  const bool full = fn->n_samples - s0 >= chunk_samples;
+  const uint64_t b_first = ((fn->s_off + s0) >> 2) * D;
+  const uint64_t b_last = b_first + (chunk_samples >> 2) * D - 1;
+  if (full && (b_first >> 32) == (b_last >> 32))
+    run_chunk<FAM, D, G, true>(fn, chunk, Q, lane);
+  else
+    run_chunk<FAM, D, G, false>(fn, chunk, Q, lane);
+}
+
+// Variant lists (family, dimension, polynomial degree or Gaussian form).
+#define ZMC_VARIANTS_DIM(X, F, G) X(F, 1, G) X(F, 2, G) X(F, 3, G) X(F, 4, G) X(F, 5, G) \
+  X(F, 6, G) X(F, 7, G)
+#define ZMC_HARMONIC_VARIANTS(X) ZMC_VARIANTS_DIM(X, ZMC_HARMONIC, 0)
+#define ZMC_ABSLIN_VARIANTS(X) ZMC_VARIANTS_DIM(X, ZMC_ABSLIN, 0)
+#define ZMC_POLY_VARIANTS(X)                                                         \
+  ZMC_VARIANTS_DIM(X, ZMC_POLY, 0) ZMC_VARIANTS_DIM(X, ZMC_POLY, 1)                  \
+  ZMC_VARIANTS_DIM(X, ZMC_POLY, 2) ZMC_VARIANTS_DIM(X, ZMC_POLY, 3)                  \
+  ZMC_VARIANTS_DIM(X, ZMC_POLY, 4)
+#define ZMC_GAUSS_VARIANTS(X) ZMC_VARIANTS_DIM(X, ZMC_GAUSS, 0) ZMC_VARIANTS_DIM(X, ZMC_GAUSS, 1)
+// switch cases of dispatch_item / dispatch_eval
+#define ZMC_ITEM_CASE(F, D, G) \
+  case variant_code(F, D, G): run_item<F, D, G>(fn, chunk, Q, lane); break;
+#define ZMC_EVAL_CASE(F, D, G) \
+  case variant_code(F, D, G): eval_range<F, D, G>(fn, s_begin, count, out); break;
+
+__device__ __forceinline__ uint32_t find_entry(const Entry *__restrict__ entries, uint32_t ne,
+                                               uint64_t item, uint32_t hint) {
+  if (hint < ne && entries[hint].item_begin <= item &&
+      (hint + 1 == ne || entries[hint + 1].item_begin > item))
+    return hint;
+  uint32_t lo = 0, hi = ne;  // invariant: entries[lo].item_begin <= item < entries[hi]
+  if (hint < ne && entries[hint].item_begin <= item) lo = hint;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (entries[mid].item_begin <= item)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// One work item (chunk) of an integrand of family FAM: switch on its variant to
+// the specialised run_item.  Specialised per family.
+template <int FAM>
+__device__ void dispatch_item(const FnDev *fn, uint64_t chunk, uint32_t Q, uint32_t lane);
+
+// Persistent, one kernel per family (so each gets the register budget of its own
+// variants): each warp takes the next work item of its family from a global
+// counter until the family's items run out; an item is one chunk of one
+// integrand.  Items are grouped by variant so co-resident warps mostly run the
+// same code.
+// Resident 256-thread blocks per SM each family kernel is compiled for (it caps
+// registers at 65536 / (256 * n)); overridable per family at build time.
+#ifndef ZMC_MIN_BLOCKS_HARMONIC
+#define ZMC_MIN_BLOCKS_HARMONIC 2
+#endif
+#ifndef ZMC_MIN_BLOCKS_ABSLIN
+#define ZMC_MIN_BLOCKS_ABSLIN 2
+#endif
+#ifndef ZMC_MIN_BLOCKS_GAUSS
+#define ZMC_MIN_BLOCKS_GAUSS 2
+#endif
+#ifndef ZMC_MIN_BLOCKS_POLY
+#define ZMC_MIN_BLOCKS_POLY 2
+#endif
+template <int FAM>
+struct MinBlocks {
+  static constexpr int value = FAM == ZMC_HARMONIC ? ZMC_MIN_BLOCKS_HARMONIC
+                               : FAM == ZMC_ABSLIN ? ZMC_MIN_BLOCKS_ABSLIN
+                               : FAM == ZMC_GAUSS  ? ZMC_MIN_BLOCKS_GAUSS
+                                                   : ZMC_MIN_BLOCKS_POLY;
+};
+
+template <int FAM>
+__global__ void __launch_bounds__(256, MinBlocks<FAM>::value)
+    zmc_batched_kernel(const Entry *__restrict__ entries,
+                                                          LaunchHdr *__restrict__ hdr) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned long long begin = hdr->item_begin[FAM];
+  const unsigned long long count = hdr->item_end[FAM] - begin;
+  const uint32_t ne = hdr->n_entries;
+  const uint32_t Q = hdr->quads_per_lane;
+  uint32_t e = 0;
+  for (;;) {
+    unsigned long long k = 0;
+    if (lane == 0) k = atomicAdd(&hdr->counter[FAM], 1ull);
+    k = __shfl_sync(kFullMask, k, 0);
+    if (k >= count) break;
+    const uint64_t item = begin + k;
+    e = find_entry(entries, ne, item, e);
+    const Entry en = entries[e];
+    dispatch_item<FAM>(en.fn, en.chunk_begin + (item - en.item_begin), Q, lane);
+  }
+}
+
+// ---------------------------------------------------------------- per-sample values
+// The scaled-back values f of samples [s_begin, s_begin + count) of one integrand,
+// from the same generator and Eval as the sampling path (parity tests).
+template <int FAM, int D, int G>
+__device__ __forceinline__ void eval_range(const FnDev *fn, uint64_t s_begin, uint32_t count,
+                                           float *out) {
+  Eval<FAM, D, G> ev;
+  ev.load(fn);
+  const RoundKeys rk = make_round_keys(fn->key0, fn->key1);
+  const uint64_t q_first = s_begin >> 2;
+  const uint64_t q_last = (s_begin + count - 1) >> 2;
+  for (uint64_t q = q_first + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+       q <= q_last; q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    uint32_t r[4 * D];
+    gen_quad<D, false>(q, 0u, 0u, fn->stream_id, rk, r);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint64_t s = 4 * q + t;
+      if (s >= s_begin && s < s_begin + count)
+        out[s - s_begin] = static_cast<float>(static_cast<double>(ev(r + t * D)) * fn->inv_scale);
+    }
+  }
+}
+
+template <int FAM>
+__device__ void dispatch_eval(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out);
+
+template <int FAM>
+__global__ void zmc_eval_kernel(const FnDev *__restrict__ fn, uint64_t s_begin, uint32_t count,
+                                float *__restrict__ out) {
+  dispatch_eval<FAM>(fn, s_begin, count, out);
+}
+
+// ---------------------------------------------------------------- host side of a family
+template <int FAM>
+cudaError_t launch_batched_family(const Entry *entries, LaunchHdr *hdr, unsigned grid,
+                                  unsigned block, cudaStream_t stream) {
+  zmc_batched_kernel<FAM><<<grid, block, 0, stream>>>(entries, hdr);
+  return cudaGetLastError();
+}
+
+template <int FAM>
+int max_blocks_family(int block) {
+  int n = 0;
+  const cudaError_t err =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zmc_batched_kernel<FAM>, block, 0);
+  return err == cudaSuccess ? n : 0;
+}
+
+template <int FAM>
+cudaError_t launch_eval_family(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out,
+                               cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  const uint64_t quads = ((s_begin + count - 1) >> 2) - (s_begin >> 2) + 1;
+  const uint64_t blocks = (quads + 255) / 256;
+  zmc_eval_kernel<FAM><<<static_cast<unsigned>(blocks < 1024 ? blocks : 1024), 256, 0, stream>>>(
+      fn, s_begin, count, out);
+  return cudaGetLastError();
+}
+
+template <int FAM>
+constexpr FamilyOps family_ops() {
+  return FamilyOps{&launch_batched_family<FAM>, &max_blocks_family<FAM>,
+                   &launch_eval_family<FAM>};
+}
+
+}  // namespace
+}  // namespace zmc

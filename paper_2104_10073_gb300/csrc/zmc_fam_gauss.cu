@@ -1,0 +1,106 @@
+// zmc_fam_gauss.cu -- the sampling path of the gauss family: its FP32
+// integrand Eval<ZMC_GAUSS, D, G>, the persistent kernel zmc_batched_kernel<ZMC_GAUSS>
+// instantiated for its variants, and the per-sample test kernel.
+#include "zmc_device.cuh"
+
+namespace zmc {
+namespace {
+
+// amp 2^-(zh + zl) for zh >= 0, |zl| << 1: the MUFU exponential of the exact
+// FP32 input -zh (measured on this part: relative error <= 1.5e-7, mean -5e-8 over
+// [-24, 0]), times the first-order correction (1 - ln2 zl).  Values below 2^-126
+// flush to zero.
+__device__ __forceinline__ float amp_exp2_neg(float amp, float zh, float zl) {
+  float e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-zh));
+  const float ae = amp * e;
+  return fmaf(ae, -0.69314718055994531f * zl, ae);
+}
+
+// A exp(-|x-mu|^2 / (2 sigma^2)) = A 2^(-Z), Z = sum_i t_i^2.  FP32 carries a
+// relative error of ~2^-24 Z in a plainly summed Z, i.e. ~Z 4e-8 in f, which
+// the tails of narrow Gaussians (Z of tens) cannot afford.  So t_i is formed as
+// an unevaluated pair th + tl (exact product th = fl(h_hi d), its rounding error,
+// and the small terms), t_i^2 as qh + c with qh = th^2 and c = (qh's error) +
+// 2 th tl, Z as zh + zl with every addition's rounding error kept (TwoSum), and
+// f = A 2^-(zh + zl).  Degree 0 / 1 select how t_i is formed (see FnDev).
+template <int D, int G>
+struct Eval<ZMC_GAUSS, D, G> {
+  float hh[D], hl[D], pa[D], pb[D];
+  float A;
+  __device__ __forceinline__ void load(const FnDev *fn) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      hh[i] = __uint_as_float(fn->w[i]);
+      hl[i] = __uint_as_float(fn->w[7 + i]);
+      pa[i] = __uint_as_float(fn->w[14 + i]);
+      pb[i] = __uint_as_float(fn->w[21 + i]);
+    }
+    A = __uint_as_float(fn->w[28]);
+  }
+  // The products and sums of the error-free transformations use the _rn
+  // intrinsics: the compiler never contracts those into an FMA, which would
+  // change the rounded value the error terms are computed against.
+  __device__ __forceinline__ float operator()(const uint32_t *r) const {
+    float zh = 0.0f, zl = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float th, tl;
+      if (G == 0) {
+        // d = v - (1 + u0): exact, the result is a multiple of 2^-23 below 2 in size
+        const float d = __fsub_rn(unit_v(r[i]), pa[i]);
+        th = __fmul_rn(hh[i], d);
+        tl = __fadd_rn(fmaf(hh[i], d, -th), fmaf(hl[i], d, pb[i]));
+      } else {
+        const float u = __fsub_rn(unit_v(r[i]), 1.0f);  // exact
+        const float ph = __fmul_rn(hh[i], u);
+        const float pl = fmaf(hh[i], u, -ph);
+        const float s = __fadd_rn(pa[i], ph);  // TwoSum(e_hi, h_hi u)
+        const float bb = __fsub_rn(s, pa[i]);
+        const float err = __fadd_rn(__fsub_rn(pa[i], __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+        th = s;
+        tl = __fadd_rn(__fadd_rn(err, pl), fmaf(hl[i], u, pb[i]));
+      }
+      const float qh = __fmul_rn(th, th);
+      const float c = fmaf(__fadd_rn(th, th), tl, fmaf(th, th, -qh));
+      if (i == 0) {
+        zh = qh;
+        zl = c;
+      } else {
+        // Fast2Sum on (max, min): both terms are >= 0, so the larger goes first
+        const float big = fmaxf(zh, qh), small = fminf(zh, qh);
+        const float s = __fadd_rn(big, small);
+        const float err = __fsub_rn(small, __fsub_rn(s, big));
+        zh = s;
+        zl = __fadd_rn(zl, __fadd_rn(err, c));
+      }
+    }
+    return amp_exp2_neg(A, zh, zl);
+  }
+};
+
+template <>
+__device__ void dispatch_item<ZMC_GAUSS>(const FnDev *fn, uint64_t chunk, uint32_t Q,
+                                      uint32_t lane) {
+  switch (fn->variant) {
+    ZMC_GAUSS_VARIANTS(ZMC_ITEM_CASE)
+    default:
+      break;
+  }
+}
+
+template <>
+__device__ void dispatch_eval<ZMC_GAUSS>(const FnDev *fn, uint64_t s_begin, uint32_t count,
+                                      float *out) {
+  switch (fn->variant) {
+    ZMC_GAUSS_VARIANTS(ZMC_EVAL_CASE)
+    default:
+      break;
+  }
+}
+
+}  // namespace
+
+const FamilyOps kFamilyGauss = family_ops<ZMC_GAUSS>();
+
+}  // namespace zmc

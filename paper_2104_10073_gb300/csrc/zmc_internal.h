@@ -1,8 +1,9 @@
 // Internal device-side layouts of the GB300 multi-function Monte Carlo path.
 //
 // The host runtime (zmc_runtime.cpp) turns each public zmc_desc into one FnDev
-// (FP32 evaluation constants derived in FP64) and the kernels (zmc_kernels.cu)
-// read only FnDev, Entry and LaunchHdr.  Nothing here is part of the C ABI.
+// (FP32 evaluation constants derived in FP64) and the kernels (zmc_kernels.cu,
+// zmc_fam_<family>.cu, zmc_plain.cu) read only FnDev, Entry, LaunchHdr and the
+// plain form's PlainFn / PlainJob.  Nothing here is part of the C ABI.
 #pragma once
 
 #include <cstddef>
@@ -67,7 +68,13 @@ struct alignas(16) FnDev {
   double inv_scale;   // 1 / S (a power of two)
   uint64_t s_off;     // absolute index of sample 0 (a multiple of 4): sample s of
                       // this descriptor is sample s_off + s of the Philox stream
-  uint32_t w[78];
+  uint32_t w[72];
+  // Moments (unscaled) of samples taken before this descriptor's, e.g. a
+  // checkpoint of the same stream; the merge combines them with this
+  // descriptor's samples (Chan).  prior_n = 0: none.
+  uint64_t prior_n;
+  double prior_mean;
+  double prior_m2;
   uint32_t out_mode;  // merge output: 0 zmc_result (estimate, stderr), 1 zmc_moments
   uint32_t reserved;
 };
@@ -114,7 +121,18 @@ struct PlainJob {
   zmc_result *out;
 };
 
-// Launch wrappers (zmc_kernels.cu).  All return the launch's cudaError_t.
+// The sampling path of one integrand family, defined in zmc_fam_<family>.cu.
+struct FamilyOps {
+  cudaError_t (*launch_batched)(const Entry *entries, LaunchHdr *hdr, unsigned grid,
+                                unsigned block, cudaStream_t stream);
+  int (*max_blocks_per_sm)(int block);  // resident blocks of `block` threads per SM
+  cudaError_t (*launch_eval)(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out,
+                             cudaStream_t stream);
+};
+extern const FamilyOps kFamilyHarmonic, kFamilyAbslin, kFamilyGauss, kFamilyPoly;
+
+// Launch wrappers (zmc_kernels.cu, zmc_plain.cu).  All return the launch's
+// cudaError_t; an unknown family gives cudaErrorInvalidValue.
 cudaError_t launch_batched(int family, const Entry *entries, LaunchHdr *hdr, unsigned grid,
                            unsigned block, cudaStream_t stream);
 cudaError_t launch_merge(const FnDev *const *fns, const LaunchHdr *hdr, unsigned grid,
@@ -124,8 +142,8 @@ cudaError_t launch_plain(const PlainFn &fn, double *block_rec, unsigned grid,
 cudaError_t launch_plain_merge(const PlainJob *jobs, uint32_t n, cudaStream_t stream);
 cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, size_t n,
                           cudaStream_t stream);
-cudaError_t launch_eval(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out,
-                        cudaStream_t stream);
+cudaError_t launch_eval(int family, const FnDev *fn, uint64_t s_begin, uint32_t count,
+                        float *out, cudaStream_t stream);
 int batched_max_blocks_per_sm(int family, int block);
 unsigned plain_grid(const PlainFn &fn, int sms);
 

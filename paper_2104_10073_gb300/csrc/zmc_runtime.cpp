@@ -1021,7 +1021,7 @@ zmc_status zmc_eval_samples(zmc_ctx *ctx, const zmc_desc *desc, uint64_t s_begin
     std::memcpy(s, &fn, sizeof fn);
     cudaError_t e = cudaMemcpyAsync(d, s, sizeof fn, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
-      e = launch_eval(reinterpret_cast<FnDev *>(d), s_begin, count,
+      e = launch_eval(static_cast<int>(desc->family), reinterpret_cast<FnDev *>(d), s_begin, count,
                       reinterpret_cast<float *>(d + sizeof(FnDev)), ctx->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(s, d + sizeof(FnDev), static_cast<size_t>(count) * 4,

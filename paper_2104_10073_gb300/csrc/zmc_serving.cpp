@@ -13,6 +13,12 @@
 //      event; two iteration slots are in flight at once;
 //   4. when a slot's event completes, hand the finished jobs' results to
 //      zmc_poll and free their device blocks.
+// Checkpoints: zmc_checkpoint takes a running job off the live list; the next
+// iteration (stream-ordered after every iteration that ran the job's chunks)
+// uploads copies of its descriptors cut to the chunks issued so far and merges
+// them into moments (out_mode 1) together with the moments the job was resumed
+// from.  zmc_submit_resume starts each integrand at sample from.n of its stream
+// (FnDev.s_off) and carries from as the descriptor's prior moments.
 // Failures: a failed CUDA call in the loop poisons the context, every pending job
 // completes with ZMC_ECUDA and later calls on the context return ZMC_ECUDA.  The
 // environment variable ZMC_SERVING_FAULT_AT=<k> injects such a failure on the
@@ -23,6 +29,7 @@
 // work list and exits.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 
@@ -34,7 +41,16 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum class JobState { kQueued, kRunning, kFinishing, kDone, kCancelled, kFailed };
+enum class JobState {
+  kQueued,
+  kRunning,
+  kFinishing,
+  kDone,
+  kCancelled,
+  kFailed,
+  kCheckpointing,  // taken off the live list; its moments merge in the next iteration
+  kCheckpointed
+};
 
 struct ServJob {
   uint64_t id = 0;
@@ -52,6 +68,7 @@ struct ServJob {
   JobState state = JobState::kQueued;
   zmc_status fail_status = ZMC_OK;
   std::vector<zmc_result> results;
+  std::vector<zmc_moments> ckpt;  // filled when a checkpoint completes
   uint64_t last_seq = 0;       // last iteration that touched the job
   Clock::time_point t_submit, t_done;
 };
@@ -82,6 +99,7 @@ struct ServingState {
   std::deque<std::shared_ptr<ServJob>> queue;
   std::vector<std::shared_ptr<ServJob>> live;
   std::deque<std::shared_ptr<ServJob>> to_merge;
+  std::deque<std::shared_ptr<ServJob>> to_ckpt;  // checkpoint merges not yet issued
   std::unordered_map<uint64_t, std::shared_ptr<ServJob>> jobs;
   std::vector<std::shared_ptr<ServJob>> cancelled_pending;
   uint64_t next_id = 1;
@@ -111,8 +129,10 @@ void free_job_device(ServingState *S, ServJob &j) {
 
 // Admission: one arena block per job; its descriptor table is copied into the
 // slot's pinned admission area and uploaded asynchronously from there.
-bool try_admit(ServingState *S, ServJob &j, char *stage, size_t &stage_used, size_t stage_cap) {
+bool try_admit(ServingState *S, const std::shared_ptr<ServJob> &jp, char *stage,
+               size_t &stage_used, size_t stage_cap) {
   zmc_ctx *ctx = S->ctx;
+  ServJob &j = *jp;
   const size_t tbytes = j.n * sizeof(FnDev);
   if (stage_used + tbytes > stage_cap) return false;
   char *blk = static_cast<char *>(ctx->arena.alloc(j.block_bytes));
@@ -138,6 +158,7 @@ bool try_admit(ServingState *S, ServJob &j, char *stage, size_t &stage_used, siz
     S->thread_status = ZMC_ECUDA;
   }
   j.state = JobState::kRunning;
+  if (j.chunks_total == 0) S->to_merge.push_back(jp);  // nothing left to sample
   return true;
 }
 
@@ -196,6 +217,19 @@ void retire_slot(ServingState *S, Slot &sl) {
       S->stats.completed++;
       S->stats.samples_done += j->samples;
       S->finished.push_back(j->id);
+    } else if (j->state == JobState::kCheckpointing) {
+      // the merge wrote moments (out_mode 1): estimate = mean, stderr_ = M2
+      const zmc_result *r =
+          reinterpret_cast<const zmc_result *>(res_base + sl.result_off[k] * sizeof(zmc_result));
+      j->ckpt.resize(j->n);
+      for (size_t i = 0; i < j->n; ++i) {
+        j->ckpt[i].mean = r[i].estimate;
+        j->ckpt[i].m2 = r[i].stderr_;
+        j->ckpt[i].n = r[i].n;
+        j->ckpt[i].status = ZMC_OK;
+        j->ckpt[i].reserved = 0;
+      }
+      j->state = JobState::kCheckpointed;
     }
     free_job_device(S, *j);
   }
@@ -235,7 +269,8 @@ void scheduler_loop(ServingState *S) {
       // fail everything that is still pending
       for (auto &kv : S->jobs)
         if (kv.second->state != JobState::kDone && kv.second->state != JobState::kCancelled &&
-            kv.second->state != JobState::kFailed) {
+            kv.second->state != JobState::kFailed &&
+            kv.second->state != JobState::kCheckpointed) {
           kv.second->state = JobState::kFailed;
           kv.second->fail_status = S->thread_status;
           S->finished.push_back(kv.first);
@@ -253,12 +288,12 @@ void scheduler_loop(ServingState *S) {
         break;
       }
     // admission in arrival order, staged through the free slot's pinned area
+    size_t used = 0;  // bytes of the slot's admission area taken this iteration
     if (slot) {
-      size_t used = 0;
       char *area = admit_area(S, *slot);
       while (!S->queue.empty()) {
         auto j = S->queue.front();
-        if (j->state == JobState::kCancelled) {
+        if (j->state == JobState::kCancelled || j->state == JobState::kCheckpointed) {
           S->queue.pop_front();
           continue;
         }
@@ -270,12 +305,12 @@ void scheduler_loop(ServingState *S) {
           S->cv_done.notify_all();
           continue;
         }
-        if (!try_admit(S, *j, area, used, kAdmitBytes)) break;
+        if (!try_admit(S, j, area, used, kAdmitBytes)) break;
         S->queue.pop_front();
         S->live.push_back(j);
       }
     }
-    const bool have_work = !S->live.empty() || !S->to_merge.empty();
+    const bool have_work = !S->live.empty() || !S->to_merge.empty() || !S->to_ckpt.empty();
     if (!slot || !have_work) {
       bool any_busy = S->slots[0].busy || S->slots[1].busy;
       if (S->stop && !any_busy) return;
@@ -325,6 +360,10 @@ void scheduler_loop(ServingState *S) {
         while (take > 0 && j->cursor < j->n && n_entries < S->max_entries) {
           const size_t i = j->cursor;
           const uint64_t left = j->nchunk[i] - j->next_chunk[i];
+          if (left == 0) {  // resumed integrand with no samples left
+            ++j->cursor;
+            continue;
+          }
           const uint64_t t = std::min(left, take);
           Entry en;
           en.item_begin = 0;  // filled when families are concatenated
@@ -400,6 +439,35 @@ void scheduler_loop(ServingState *S) {
       j->state = JobState::kFinishing;
       j->last_seq = seq;
       S->to_merge.pop_front();
+    }
+    // checkpoints: descriptors cut to the chunks issued so far, merged into moments
+    while (!S->to_ckpt.empty()) {
+      auto j = S->to_ckpt.front();
+      if (j->state != JobState::kCheckpointing) {
+        S->to_ckpt.pop_front();
+        continue;
+      }
+      const size_t tbytes = j->n * sizeof(FnDev);
+      if (nm + j->n > S->max_merge || used + tbytes > kAdmitBytes) break;
+      const uint64_t chunk = 128ull * ctx->quads_per_lane;
+      FnDev *cut = reinterpret_cast<FnDev *>(admit_area(S, *slot) + used);
+      for (size_t i = 0; i < j->n; ++i) {
+        cut[i] = j->fns[i];
+        cut[i].n_samples = std::min(j->next_chunk[i] * chunk, j->fns[i].n_samples);
+        cut[i].out_mode = 1;
+        mrg[nm + i] = j->d_fns + i;
+      }
+      used += round256(tbytes);
+      cudaError_t e = cudaMemcpyAsync(j->d_fns, cut, tbytes, cudaMemcpyHostToDevice, S->stream);
+      if (e != cudaSuccess) {
+        ctx_cuda_fail(ctx, e, "serving checkpoint upload");
+        S->thread_status = ZMC_ECUDA;
+      }
+      slot->finishing.push_back(j);
+      slot->result_off.push_back(nm);
+      nm += static_cast<uint32_t>(j->n);
+      j->last_seq = seq;
+      S->to_ckpt.pop_front();
     }
     hdr->n_merge = nm;
     // drop finished jobs from the live list
@@ -495,8 +563,12 @@ void serving_stop(zmc_ctx *ctx) {
     for (auto &j : S->live) j->state = JobState::kCancelled;
     S->live.clear();
     S->to_merge.clear();
+    for (auto &j : S->to_ckpt)
+      if (j->state == JobState::kCheckpointing) j->state = JobState::kCancelled;
+    S->to_ckpt.clear();
   }
   S->cv_work.notify_all();
+  S->cv_done.notify_all();
   if (S->thread.joinable()) S->thread.join();
   cudaStreamSynchronize(S->stream);
   for (auto &kv : S->jobs) free_job_device(S, *kv.second);
@@ -513,9 +585,12 @@ void serving_stop(zmc_ctx *ctx) {
   ctx->srv = nullptr;
 }
 
-extern "C" {
+namespace {
 
-zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *job_id) {
+// Validate, precompute and queue a job; from (optional) holds per-integrand
+// moments of samples [0, from[i].n) of its stream, taken earlier.
+zmc_status submit_job(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *from, size_t n,
+                      uint64_t *job_id) {
   if (!ctx || !desc || !job_id || n == 0) return set_error(ZMC_EINVAL, "bad submit arguments");
   if (!ctx->serving || !ctx->srv) return set_error(ZMC_EINVAL, "context created without serving");
   if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
@@ -530,10 +605,27 @@ zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *jo
   for (size_t i = 0; i < n; ++i) {
     zmc_status st = precompute(desc[i], &j->fns[i], nullptr, nullptr);
     if (st != ZMC_OK) return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    uint64_t start = 0;
+    if (from && from[i].n > 0) {
+      const zmc_moments &m = from[i];
+      start = m.n;
+      if (m.status != ZMC_OK || start > desc[i].n_samples ||
+          (start % 4 != 0 && start != desc[i].n_samples) || !std::isfinite(m.mean) ||
+          !std::isfinite(m.m2) || m.m2 < 0.0)
+        return set_error(ZMC_EINVAL,
+                         "descriptor %zu: resume moments need status OK, finite mean and "
+                         "M2 >= 0, n <= n_samples and n a multiple of 4 (or n_samples)", i);
+      FnDev &f = j->fns[i];
+      f.s_off = start;
+      f.n_samples = desc[i].n_samples - start;
+      f.prior_n = start;
+      f.prior_mean = m.mean;
+      f.prior_m2 = m.m2;
+    }
     j->family[i] = static_cast<int>(desc[i].family);
-    j->nchunk[i] = (desc[i].n_samples + chunk - 1) / chunk;
+    j->nchunk[i] = (desc[i].n_samples - start + chunk - 1) / chunk;
     j->chunks_total += j->nchunk[i];
-    j->samples += desc[i].n_samples;
+    j->samples += desc[i].n_samples - start;
   }
   j->block_bytes = round256(n * sizeof(FnDev)) + round256(j->chunks_total * sizeof(float2)) +
                    round256(n * sizeof(zmc_result));
@@ -556,6 +648,20 @@ zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *jo
   return ZMC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *job_id) {
+  return submit_job(ctx, desc, nullptr, n, job_id);
+}
+
+zmc_status zmc_submit_resume(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *from,
+                             size_t n, uint64_t *job_id) {
+  if (!from) return set_error(ZMC_EINVAL, "null moments");
+  return submit_job(ctx, desc, from, n, job_id);
+}
+
 zmc_status zmc_poll(zmc_ctx *ctx, uint64_t job_id, zmc_result *out, int32_t wait_ms) {
   if (!ctx || !ctx->srv) return set_error(ZMC_EINVAL, "context created without serving");
   ServingState *S = ctx->srv;
@@ -566,7 +672,7 @@ zmc_status zmc_poll(zmc_ctx *ctx, uint64_t job_id, zmc_result *out, int32_t wait
   std::shared_ptr<ServJob> j = it->second;
   auto finished = [&] {
     return j->state == JobState::kDone || j->state == JobState::kCancelled ||
-           j->state == JobState::kFailed;
+           j->state == JobState::kFailed || j->state == JobState::kCheckpointed;
   };
   if (!finished()) {
     if (wait_ms == 0) return set_error(ZMC_EAGAIN, "job not finished");
@@ -578,6 +684,8 @@ zmc_status zmc_poll(zmc_ctx *ctx, uint64_t job_id, zmc_result *out, int32_t wait
   }
   S->jobs.erase(job_id);
   if (j->state == JobState::kCancelled) return set_error(ZMC_ECLOSED, "job was cancelled");
+  if (j->state == JobState::kCheckpointed)
+    return set_error(ZMC_ECLOSED, "job was checkpointed");
   if (j->state == JobState::kFailed) return set_error(j->fail_status, "job failed");
   if (out) std::memcpy(out, j->results.data(), j->n * sizeof(zmc_result));
   return ZMC_OK;
@@ -590,10 +698,13 @@ zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id) {
   auto it = S->jobs.find(job_id);
   if (it == S->jobs.end()) return set_error(ZMC_ENOTFOUND, "unknown job");
   auto &j = it->second;
-  if (j->state == JobState::kDone || j->state == JobState::kFailed) return ZMC_OK;
+  if (j->state == JobState::kDone || j->state == JobState::kFailed ||
+      j->state == JobState::kCancelled || j->state == JobState::kCheckpointed)
+    return ZMC_OK;
   if (j->state == JobState::kQueued) {
     j->state = JobState::kCancelled;
-  } else if (j->state == JobState::kRunning || j->state == JobState::kFinishing) {
+  } else if (j->state == JobState::kRunning || j->state == JobState::kFinishing ||
+             j->state == JobState::kCheckpointing) {
     j->state = JobState::kCancelled;
     // device memory is freed once the last iteration that used it has finished
     S->cancelled_pending.push_back(j);
@@ -602,6 +713,65 @@ zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id) {
   S->stats.cancelled++;
   S->finished.push_back(job_id);
   S->cv_done.notify_all();
+  return ZMC_OK;
+}
+
+zmc_status zmc_checkpoint(zmc_ctx *ctx, uint64_t job_id, zmc_moments *out, int32_t wait_ms) {
+  if (!ctx || !ctx->srv) return set_error(ZMC_EINVAL, "context created without serving");
+  if (!out) return set_error(ZMC_EINVAL, "null output");
+  ServingState *S = ctx->srv;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(job_id);
+  if (it == S->jobs.end()) return set_error(ZMC_ENOTFOUND, "unknown job %llu",
+                                            static_cast<unsigned long long>(job_id));
+  std::shared_ptr<ServJob> j = it->second;
+  switch (j->state) {
+    case JobState::kQueued:
+      // nothing ran: the moments it started from
+      for (size_t i = 0; i < j->n; ++i) {
+        const FnDev &f = j->fns[i];
+        out[i].mean = f.prior_n ? f.prior_mean : 0.0;
+        out[i].m2 = f.prior_n ? f.prior_m2 : 0.0;
+        out[i].n = f.prior_n;
+        out[i].status = ZMC_OK;
+        out[i].reserved = 0;
+      }
+      j->state = JobState::kCheckpointed;
+      S->jobs.erase(job_id);
+      S->cv_done.notify_all();
+      return ZMC_OK;
+    case JobState::kRunning:
+      if (j->chunks_issued == j->chunks_total)
+        return set_error(ZMC_EAGAIN, "job has issued all of its samples; collect it with zmc_poll");
+      j->state = JobState::kCheckpointing;
+      S->live.erase(std::remove(S->live.begin(), S->live.end(), j), S->live.end());
+      S->to_ckpt.push_back(j);
+      S->cv_work.notify_one();
+      break;
+    case JobState::kCheckpointing:
+    case JobState::kCheckpointed:
+      break;
+    case JobState::kFinishing:
+    case JobState::kDone:
+      return set_error(ZMC_EAGAIN, "job has issued all of its samples; collect it with zmc_poll");
+    case JobState::kCancelled:
+      return set_error(ZMC_ECLOSED, "job was cancelled");
+    case JobState::kFailed:
+      return set_error(j->fail_status, "job failed");
+  }
+  auto settled = [&] { return j->state != JobState::kCheckpointing; };
+  if (!settled()) {
+    if (wait_ms == 0) return set_error(ZMC_EAGAIN, "checkpoint under way");
+    if (wait_ms < 0) {
+      S->cv_done.wait(lk, settled);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), settled)) {
+      return set_error(ZMC_ETIMEOUT, "checkpoint not finished after %d ms", wait_ms);
+    }
+  }
+  if (j->state == JobState::kCancelled) return set_error(ZMC_ECLOSED, "job was cancelled");
+  if (j->state == JobState::kFailed) return set_error(j->fail_status, "job failed");
+  std::memcpy(out, j->ckpt.data(), j->n * sizeof(zmc_moments));
+  S->jobs.erase(job_id);
   return ZMC_OK;
 }
 

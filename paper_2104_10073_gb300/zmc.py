@@ -79,6 +79,9 @@ _SIGS = {
     "zmc_submit": ([_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "zmc_poll": ([_P, ctypes.c_uint64, _P, ctypes.c_int32], ctypes.c_int),
     "zmc_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "zmc_checkpoint": ([_P, ctypes.c_uint64, _P, ctypes.c_int32], ctypes.c_int),
+    "zmc_submit_resume": ([_P, _P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)],
+                          ctypes.c_int),
     "zmc_poll_any": ([_P, _P, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)],
                      ctypes.c_int),
     "zmc_serving_stats_get": ([_P, ctypes.POINTER(zmc_serving_stats)], ctypes.c_int),
@@ -238,6 +241,26 @@ def zmc_poll_any(ctx: int, cap: int = 1024, wait_ms: int = -1):
 
 def zmc_cancel(ctx: int, job_id: int) -> None:
     _check(lib().zmc_cancel(ctx, job_id), "zmc_cancel")
+
+
+def zmc_checkpoint(ctx: int, job_id: int, n: int, wait_ms: int = -1):
+    """(status, moments-or-None): stop a job and take the moments of the samples
+    each of its n integrands has taken; ZMC_EAGAIN / ZMC_ETIMEOUT are not errors."""
+    out = np.zeros(n, dtype=MOMENTS_DTYPE)
+    st = lib().zmc_checkpoint(ctx, job_id, out.ctypes.data, wait_ms)
+    return st, (out if st == ZMC_OK else None)
+
+
+def zmc_submit_resume(ctx: int, desc, from_moments) -> int:
+    """Submit ``desc`` continuing from ``from_moments`` (a zmc_checkpoint result,
+    or zmc_integrate_moments over samples [0, n) of the same streams)."""
+    t = _table(desc)
+    m = np.ascontiguousarray(np.asarray(from_moments, dtype=MOMENTS_DTYPE).reshape(-1))
+    assert len(m) == len(t)
+    jid = ctypes.c_uint64()
+    _check(lib().zmc_submit_resume(ctx, t.ctypes.data, m.ctypes.data, len(t), ctypes.byref(jid)),
+           "zmc_submit_resume")
+    return jid.value
 
 
 def zmc_serving_stats_get(ctx: int) -> dict:
