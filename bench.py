@@ -349,10 +349,11 @@ def run_native(args, world, rank, local):
             mixed["batched_over_plain"] = mixed["batched_gsps"] / mixed["plain_gsps"]
         zmc.zmc_plan_destroy(mp)
 
-    functional = checkpoint = None
+    functional = checkpoint = udf = None
     if rank == 0 and not args.skip_modes:
         functional = run_functional(zmc, ctx)
         checkpoint = run_checkpoint(zmc, local, ctx)
+        udf = run_udf(zmc, ctx)
 
     serving = None
     if rank == 0 and not args.skip_serving:
@@ -385,6 +386,7 @@ def run_native(args, world, rank, local):
         "mixed": mixed,
         "functional": functional,
         "checkpoint": checkpoint,
+        "udf": udf,
         "serving": serving,
         "e2e": None if e2e_s is None else {
             "value": total / e2e_s / 1e9, "unit": UNIT,
@@ -511,6 +513,42 @@ def run_checkpoint(zmc, device, ref_ctx):
             "max_abs_diff_in_stderr": float(dev.max())}
 
 
+def run_udf(zmc, ctx):
+    """User-defined integrands compiled at run time: the Fig. 1 x 10 table
+    (10^9 samples) with Eq. 1 written as user code, FP32 (sincosf) and FP64
+    (cos, sin), end to end through Udf.integrate; compile time reported apart."""
+    tab = W.harmonic_fig1(10**6, seeds=range(10))
+    tab["family"] = W.USER
+    srcs = {
+        "f32": ("__device__ float zmc_user_f(const float *x, const float *p) {\n"
+                "  float ph = 0.0f;\n"
+                "  for (int i = 0; i < ZMC_UDF_DIM; ++i) ph = fmaf(p[2 + i], x[i], ph);\n"
+                "  float s, c; sincosf(ph, &s, &c); return p[0] * c + p[1] * s;\n}\n",
+                zmc.ZMC_UDF_F32),
+        "f64": ("__device__ double zmc_user_f(const double *x, const double *p) {\n"
+                "  double ph = 0.0;\n"
+                "  for (int i = 0; i < ZMC_UDF_DIM; ++i) ph = fma(p[2 + i], x[i], ph);\n"
+                "  return p[0] * cos(ph) + p[1] * sin(ph);\n}\n", zmc.ZMC_UDF_F64),
+    }
+    out = {"workload": "fig1-harmonics-100x1e6-x10-repeats as user code", "samples": 10**9}
+    for name, (src, prec) in srcs.items():
+        t0 = time.perf_counter()
+        u = zmc.Udf(src, 4, prec, amplitude=2.0)
+        compile_s = time.perf_counter() - t0
+        u.integrate(ctx.handle, tab)  # load + warm-up
+        t = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            res = u.integrate(ctx.handle, tab)
+            t.append(time.perf_counter() - t0)
+        assert np.all(res["status"] == 0)
+        sec = statistics.median(t)
+        out[name] = {"value": 1e9 / sec / 1e9, "unit": UNIT, "ms": 1e3 * sec,
+                     "compile_s": compile_s}
+        u.close()
+    return out
+
+
 def run_serving_sweep(args):
     """p50/p99 job latency and throughput over a sweep of Poisson arrival rates
     (rank 0, one GPU); one JSON object on stdout."""
@@ -540,7 +578,7 @@ def main():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-modes", action="store_true",
-                    help="skip the functional-mode and checkpoint/resume legs")
+                    help="skip the functional-mode, checkpoint/resume and user-integrand legs")
     ap.add_argument("--cpu-repeats", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-sweep", action="store_true")

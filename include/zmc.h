@@ -48,7 +48,13 @@ extern "C" {
  *   ZMC_ABSLIN    a |c.x|                        (Eq. 2)   p[0]=a p[1+i]=c_i
  *   ZMC_GAUSS     A exp(-|x-mu|^2 / (2 sigma^2))           p[0]=A p[1]=sigma p[2+i]=mu_i
  *   ZMC_POLY      prod_i sum_{j<=deg} c_ij x_i^j          p[5i+j]=c_ij              */
-enum zmc_family { ZMC_HARMONIC = 0, ZMC_ABSLIN = 1, ZMC_GAUSS = 2, ZMC_POLY = 3 };
+enum zmc_family {
+    ZMC_HARMONIC = 0,
+    ZMC_ABSLIN = 1,
+    ZMC_GAUSS = 2,
+    ZMC_POLY = 3,
+    ZMC_USER = 4 /* a user-defined integrand: only through zmc_udf_integrate        */
+};
 
 typedef enum zmc_status {
     ZMC_OK = 0,
@@ -288,6 +294,56 @@ zmc_status zmc_philox4x32_10(zmc_ctx *ctx, const uint32_t *ctr, const uint32_t *
  * evaluation code; out has count floats (host). */
 zmc_status zmc_eval_samples(zmc_ctx *ctx, const zmc_desc *desc, uint64_t s_begin,
                             uint32_t count, float *out);
+
+/* ---- User-defined integrands, compiled at run time ----------------------------
+ * The paper's integrators take the integrand as a user-written function that
+ * is compiled for the GPU (Sec. "Summary of revisions" and "Solution method":
+ * the multi-function mode integrates functions of different forms, dimensions
+ * and domains).  zmc_udf_create compiles `source` (CUDA C++, NUL-terminated) with
+ * NVRTC for this GPU; the source must define, for precision ZMC_UDF_F32:
+ *     __device__ float  zmc_user_f(const float *x, const float *p)
+ * or, for ZMC_UDF_F64:
+ *     __device__ double zmc_user_f(const double *x, const double *p)
+ * x is the sample point (dim coordinates), p the descriptor's ZMC_NPARAM
+ * parameters (zmc_desc.p, rounded to float for ZMC_UDF_F32).  The macros
+ * ZMC_UDF_DIM and ZMC_UDF_PRECISION are defined for the source.  The library
+ * supplies the rest of the path -- the same Philox4x32-10 words and box map as
+ * the built-in families (so a user form of a built-in integrand sees exactly
+ * the same samples), FP32 per-chunk sums of S f and the FP64 merge.
+ *   ZMC_UDF_F32: map x_i = lo_i + w_i u_i and f in FP32 (fastest; the user's
+ *                FP32 arithmetic decides the accuracy of f).
+ *   ZMC_UDF_F64: map and f in FP64, each value rounded to FP32 before the sums
+ *                (relative error 2^-24 per sample; slower on GB300's FP64 rate).
+ * `amplitude` > 0 is an upper bound of |f| over every box the udf integrates;
+ * the library then sums S f with S = 2^(48 - ceil(log2 amplitude)) so that
+ * values down to ~2^-111 amplitude keep their squares in FP32 range (0: S = 1,
+ * fine for |f| within about [1e-18, 1e18]).
+ * Returns ZMC_EINVAL with the start of the compiler log in zmc_last_error() if
+ * the source does not compile, ZMC_ENOSYS if NVRTC cannot be loaded.  Needs no
+ * GPU and no context; the compiled image is loaded on a device at first use.  */
+#define ZMC_UDF_F32 0u
+#define ZMC_UDF_F64 1u
+typedef struct zmc_udf zmc_udf;
+zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
+                          double amplitude, zmc_udf **out);
+
+/* Integrate n descriptors (host array) with a compiled user integrand: every
+ * desc[i].family must be ZMC_USER and desc[i].dim the udf's dimension (deg is
+ * ignored; box, samples, seed, stream and p as for the built-in families).
+ * Results (host array) as zmc_integrate's.  Blocking, on the context's stream. */
+zmc_status zmc_udf_integrate(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc *desc,
+                             size_t n, zmc_result *out);
+
+/* FP32 values f(x_s), s in [s_begin, s_begin + count), of one descriptor, from
+ * the same generation, map and evaluation as zmc_udf_integrate (for tests). */
+zmc_status zmc_udf_eval_samples(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc *desc,
+                                uint64_t s_begin, uint32_t count, float *out);
+
+/* The NVRTC log of the udf's compilation (warnings; "" if none). */
+const char *zmc_udf_log(const zmc_udf *udf);
+
+/* Release a udf (NULL accepted).  Not while a call using it is running. */
+zmc_status zmc_udf_destroy(zmc_udf *udf);
 
 /* ---- Integration without allocation (the paper has no counterpart) -------------
  * For callers that must not allocate device memory when they need a result: a

@@ -24,8 +24,14 @@ BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["zmc_fam_harmonic.cu", "zmc_fam_abslin.cu", "zmc_fam_gauss.cu", "zmc_fam_poly.cu",
            "zmc_plain.cu", "zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp",
-           "zmc_noalloc.cu", "zmc_tune.cpp"]
-HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h", "zmc_device.cuh"]
+           "zmc_noalloc.cu", "zmc_tune.cpp", "zmc_udf.cpp"]
+HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h", "zmc_device.cuh",
+           "zmc_udf_kernel.cuh"]
+# Headers whose text zmc_udf.cpp hands to NVRTC (symbol name, path).
+JIT_HEADERS = [("kJitZmcH", os.path.join(INCLUDE, "zmc.h")),
+               ("kJitZmcInternalH", os.path.join(CSRC, "zmc_internal.h")),
+               ("kJitZmcDeviceCuh", os.path.join(CSRC, "zmc_device.cuh")),
+               ("kJitZmcUdfKernelCuh", os.path.join(CSRC, "zmc_udf_kernel.cuh"))]
 
 
 def _nvcc() -> str:
@@ -40,7 +46,23 @@ def _flags(extra=()):
     # multiply form) for sweeps; the defaults are the tuned values.
     defs = os.environ.get("ZMC_NVCC_DEFINES", "").split()
     return [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-            "-I", CSRC, *defs, *extra]
+            "-I", CSRC, "-I", BUILD, *defs, *extra]
+
+
+def _write_jit_sources() -> None:
+    """_build/zmc_jit_sources.h: the headers of the run-time compiled path as
+    C string constants (raw literals, one per header)."""
+    out = ["// Generated by build.py from the headers named below; do not edit.", "#pragma once"]
+    for sym, path in JIT_HEADERS:
+        text = open(path).read()
+        assert ')zmcjit"' not in text
+        out.append(f"// {os.path.relpath(path, ROOT)}")
+        out.append(f'static const char {sym}[] = R"zmcjit({text})zmcjit";')
+    data = "\n".join(out) + "\n"
+    path = os.path.join(BUILD, "zmc_jit_sources.h")
+    if not os.path.exists(path) or open(path).read() != data:
+        with open(path, "w") as f:
+            f.write(data)
 
 
 def _newest_input() -> float:
@@ -54,6 +76,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= _newest_input():
         return OUT
     os.makedirs(BUILD, exist_ok=True)
+    _write_jit_sources()
     nvcc = _nvcc()
 
     def compile_one(src):
@@ -72,7 +95,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = OUT + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-cudart", "static", *objs, "-o", tmp,
-           "-lpthread"]
+           "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

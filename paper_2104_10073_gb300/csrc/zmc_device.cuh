@@ -14,6 +14,9 @@
 
 #include "zmc_internal.h"
 
+// Also compiled at run time by NVRTC for user-defined integrands (zmc_udf.cpp):
+// the host-side launch helpers at the end are hidden from it.
+
 namespace zmc {
 namespace {
 
@@ -307,19 +310,26 @@ struct MinBlocks {
                                                    : ZMC_MIN_BLOCKS_POLY;
 };
 
+// The LaunchHdr slot a family's kernel drains: its own for the built-in
+// families, slot 0 of a launch of its own for a user-defined integrand.
 template <int FAM>
-__global__ void __launch_bounds__(256, MinBlocks<FAM>::value)
-    zmc_batched_kernel(const Entry *__restrict__ entries,
-                                                          LaunchHdr *__restrict__ hdr) {
+struct HdrSlot {
+  static constexpr int value = FAM < 4 ? FAM : 0;
+};
+
+template <int FAM>
+__device__ __forceinline__ void batched_loop(const Entry *__restrict__ entries,
+                                             LaunchHdr *__restrict__ hdr) {
+  constexpr int kSlot = HdrSlot<FAM>::value;
   const uint32_t lane = threadIdx.x & 31u;
-  const unsigned long long begin = hdr->item_begin[FAM];
-  const unsigned long long count = hdr->item_end[FAM] - begin;
+  const unsigned long long begin = hdr->item_begin[kSlot];
+  const unsigned long long count = hdr->item_end[kSlot] - begin;
   const uint32_t ne = hdr->n_entries;
   const uint32_t Q = hdr->quads_per_lane;
   uint32_t e = 0;
   for (;;) {
     unsigned long long k = 0;
-    if (lane == 0) k = atomicAdd(&hdr->counter[FAM], 1ull);
+    if (lane == 0) k = atomicAdd(&hdr->counter[kSlot], 1ull);
     k = __shfl_sync(kFullMask, k, 0);
     if (k >= count) break;
     const uint64_t item = begin + k;
@@ -327,6 +337,12 @@ __global__ void __launch_bounds__(256, MinBlocks<FAM>::value)
     const Entry en = entries[e];
     dispatch_item<FAM>(en.fn, en.chunk_begin + (item - en.item_begin), Q, lane);
   }
+}
+
+template <int FAM>
+__global__ void __launch_bounds__(256, MinBlocks<FAM>::value)
+    zmc_batched_kernel(const Entry *__restrict__ entries, LaunchHdr *__restrict__ hdr) {
+  batched_loop<FAM>(entries, hdr);
 }
 
 // ---------------------------------------------------------------- per-sample values
@@ -362,6 +378,7 @@ __global__ void zmc_eval_kernel(const FnDev *__restrict__ fn, uint64_t s_begin, 
   dispatch_eval<FAM>(fn, s_begin, count, out);
 }
 
+#ifndef __CUDACC_RTC__
 // ---------------------------------------------------------------- host side of a family
 template <int FAM>
 cudaError_t launch_batched_family(const Entry *entries, LaunchHdr *hdr, unsigned grid,
@@ -394,6 +411,8 @@ constexpr FamilyOps family_ops() {
   return FamilyOps{&launch_batched_family<FAM>, &max_blocks_family<FAM>,
                    &launch_eval_family<FAM>};
 }
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace
 }  // namespace zmc

@@ -6,6 +6,9 @@
 // plain form's PlainFn / PlainJob.  Nothing here is part of the C ABI.
 #pragma once
 
+// This header is also compiled at run time by NVRTC for user-defined integrands
+// (zmc_udf.cpp supplies minimal <cstdint>, <cstddef> and <cuda_runtime.h>);
+// host-only declarations are hidden from it.
 #include <cstddef>
 #include <cstdint>
 
@@ -121,6 +124,7 @@ struct PlainJob {
   zmc_result *out;
 };
 
+#ifndef __CUDACC_RTC__
 // The sampling path of one integrand family, defined in zmc_fam_<family>.cu.
 struct FamilyOps {
   cudaError_t (*launch_batched)(const Entry *entries, LaunchHdr *hdr, unsigned grid,
@@ -146,5 +150,6 @@ cudaError_t launch_eval(int family, const FnDev *fn, uint64_t s_begin, uint32_t 
                         float *out, cudaStream_t stream);
 int batched_max_blocks_per_sm(int family, int block);
 unsigned plain_grid(const PlainFn &fn, int sms);
+#endif  // __CUDACC_RTC__
 
 }  // namespace zmc

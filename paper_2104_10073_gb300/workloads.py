@@ -42,6 +42,7 @@ MAX_DIM = 7
 N_PARAM = 40
 
 HARMONIC, ABSLIN, GAUSS, POLY = 0, 1, 2, 3
+USER = 4  # a user-defined integrand (zmc_udf_integrate)
 FAMILY_NAMES = {HARMONIC: "harmonic", ABSLIN: "abslin", GAUSS: "gauss", POLY: "poly"}
 
 DESC_DTYPE = np.dtype(

@@ -29,6 +29,8 @@ STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_EAGAIN",
                 4: "ZMC_ETIMEOUT", 5: "ZMC_ECUDA", 6: "ZMC_ENOTFOUND", 7: "ZMC_ECLOSED",
                 8: "ZMC_ENOSYS"}
 ZMC_STAGE_SAMPLE, ZMC_STAGE_MERGE, ZMC_STAGE_ALL = 1, 2, 3
+ZMC_USER = 4
+ZMC_UDF_F32, ZMC_UDF_F64 = 0, 1
 
 RESULT_DTYPE = np.dtype([("estimate", "<f8"), ("stderr", "<f8"), ("n", "<u8"),
                          ("status", "<i4"), ("reserved", "<i4")])
@@ -96,6 +98,12 @@ _SIGS = {
     "zmc_eval_samples": ([_P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_validate": ([_P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "zmc_integrate_noalloc": ([_P, ctypes.c_size_t, _P, _P], ctypes.c_int),
+    "zmc_udf_create": ([ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                        ctypes.POINTER(_P)], ctypes.c_int),
+    "zmc_udf_integrate": ([_P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "zmc_udf_eval_samples": ([_P, _P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
+    "zmc_udf_log": ([_P], ctypes.c_char_p),
+    "zmc_udf_destroy": ([_P], ctypes.c_int),
     "zmc_desc_size": ([], ctypes.c_size_t),
     "zmc_result_size": ([], ctypes.c_size_t),
 }
@@ -347,6 +355,51 @@ def zmc_validate(desc):
 
 
 # ------------------------------------------------------------------ convenience
+class Udf:
+    """A user-defined integrand compiled at run time (NVRTC); see zmc_udf_create.
+
+    ``source`` defines ``zmc_user_f(const float *x, const float *p)`` (precision
+    ZMC_UDF_F32) or the ``double`` form (ZMC_UDF_F64).  Compiling needs no GPU."""
+
+    def __init__(self, source: str, dim: int, precision: int = ZMC_UDF_F32,
+                 amplitude: float = 0.0):
+        h = _P()
+        _check(lib().zmc_udf_create(source.encode(), dim, precision, amplitude, ctypes.byref(h)),
+               "zmc_udf_create")
+        self.handle = h.value
+        self.dim = dim
+        self.precision = precision
+
+    @property
+    def log(self) -> str:
+        return lib().zmc_udf_log(self.handle).decode()
+
+    def integrate(self, ctx: int, desc) -> np.ndarray:
+        t = _table(desc)
+        out = np.zeros(len(t), dtype=RESULT_DTYPE)
+        _check(lib().zmc_udf_integrate(ctx, self.handle, t.ctypes.data, len(t), out.ctypes.data),
+               "zmc_udf_integrate")
+        return out
+
+    def eval_samples(self, ctx: int, row, s_begin: int, count: int) -> np.ndarray:
+        t = _table(np.asarray(row).reshape(1))
+        out = np.zeros(count, dtype=np.float32)
+        _check(lib().zmc_udf_eval_samples(ctx, self.handle, t.ctypes.data, s_begin, count,
+                                          out.ctypes.data), "zmc_udf_eval_samples")
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().zmc_udf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """A library context whose device memory and stream come from PyTorch.
 

@@ -69,6 +69,8 @@ def sample_scale(row) -> float:
     """A bound on |f| over the box, for per-sample comparisons."""
     fam, d = int(row["family"]), int(row["dim"])
     lo, hi, p = row["lo"][:d], row["hi"][:d], row["p"]
+    if fam == W.USER:  # no bound is known for a user-defined integrand
+        return 0.0
     if fam == W.HARMONIC:
         return abs(p[0]) + abs(p[1])
     if fam == W.ABSLIN:
