@@ -349,11 +349,12 @@ def run_native(args, world, rank, local):
             mixed["batched_over_plain"] = mixed["batched_gsps"] / mixed["plain_gsps"]
         zmc.zmc_plan_destroy(mp)
 
-    functional = checkpoint = udf = None
+    functional = checkpoint = udf = normal = None
     if rank == 0 and not args.skip_modes:
         functional = run_functional(zmc, ctx)
         checkpoint = run_checkpoint(zmc, local, ctx)
         udf = run_udf(zmc, ctx)
+        normal = run_normal(zmc, ctx)
 
     serving = None
     if rank == 0 and not args.skip_serving:
@@ -387,6 +388,7 @@ def run_native(args, world, rank, local):
         "functional": functional,
         "checkpoint": checkpoint,
         "udf": udf,
+        "normal": normal,
         "serving": serving,
         "e2e": None if e2e_s is None else {
             "value": total / e2e_s / 1e9, "unit": UNIT,
@@ -549,6 +551,35 @@ def run_udf(zmc, ctx):
     return out
 
 
+def run_normal(zmc, ctx):
+    """Stratified sampling with tree refinement (the paper's normal mode, for 8 to
+    12 dimensions) on the case it is meant for, a localised integrand: a 10-D
+    Gaussian peak (sigma 0.1 at (0.25, ..., 0.25)) as run-time compiled user code
+    on [0, 1]^10; 2^10 level-0 cells x 2^14 samples, up to two refinement
+    rounds; against plain direct MC with the same number of samples (one cell)."""
+    src = ("__device__ float zmc_user_f(const float *x, const float *p) {\n"
+           "  float r2 = 0.0f;\n"
+           "  for (int i = 0; i < ZMC_UDF_DIM; ++i) r2 = fmaf(x[i] - p[0], x[i] - p[0], r2);\n"
+           "  return expf(-r2 / (2.0f * p[1] * p[1]));\n}\n")
+    u = zmc.Udf(src, 10, zmc.ZMC_UDF_F32, amplitude=1.0)
+    lo, hi, p = np.zeros(10), np.ones(10), np.array([0.25, 0.1])
+    opts = zmc.normal_options(divisions=2, depth=2, samples_per_cell=1 << 14, sigma_mult=3.0,
+                              seed=1, max_leaves=8 << 10)
+    u.normal_integrate(ctx.handle, lo, hi, p, opts)  # load + warm-up
+    t0 = time.perf_counter()
+    r = u.normal_integrate(ctx.handle, lo, hi, p, opts)
+    sec = time.perf_counter() - t0
+    plain = u.normal_integrate(ctx.handle, lo, hi, p, zmc.normal_options(
+        divisions=1, depth=0, samples_per_cell=r["n_samples"], seed=1, stream_base=1 << 20))
+    u.close()
+    return {"workload": "gauss-peak-10d-user-code, 2^10 cells x 2^14, depth 2",
+            "value": r["n_samples"] / sec / 1e9, "unit": UNIT, "ms": 1e3 * sec,
+            "samples": r["n_samples"], "cells": r["n_cells"], "leaves": r["n_leaves"],
+            "rounds": r["rounds"], "estimate": r["estimate"], "stderr": r["stderr"],
+            "plain_estimate": plain["estimate"], "plain_stderr": plain["stderr"],
+            "variance_reduction": (plain["stderr"] / r["stderr"]) ** 2}
+
+
 def run_serving_sweep(args):
     """p50/p99 job latency and throughput over a sweep of Poisson arrival rates
     (rank 0, one GPU); one JSON object on stdout."""
@@ -578,7 +609,8 @@ def main():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-modes", action="store_true",
-                    help="skip the functional-mode, checkpoint/resume and user-integrand legs")
+                    help="skip the functional, checkpoint/resume, user-integrand and "
+                         "stratified (normal-mode) legs")
     ap.add_argument("--cpu-repeats", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-sweep", action="store_true")

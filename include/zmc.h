@@ -304,7 +304,7 @@ zmc_status zmc_eval_samples(zmc_ctx *ctx, const zmc_desc *desc, uint64_t s_begin
  *     __device__ float  zmc_user_f(const float *x, const float *p)
  * or, for ZMC_UDF_F64:
  *     __device__ double zmc_user_f(const double *x, const double *p)
- * x is the sample point (dim coordinates), p the descriptor's ZMC_NPARAM
+ * x is the sample point (dim coordinates, dim 1..12), p the descriptor's ZMC_NPARAM
  * parameters (zmc_desc.p, rounded to float for ZMC_UDF_F32).  The macros
  * ZMC_UDF_DIM and ZMC_UDF_PRECISION are defined for the source.  The library
  * supplies the rest of the path -- the same Philox4x32-10 words and box map as
@@ -328,9 +328,11 @@ zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
                           double amplitude, zmc_udf **out);
 
 /* Integrate n descriptors (host array) with a compiled user integrand: every
- * desc[i].family must be ZMC_USER and desc[i].dim the udf's dimension (deg is
- * ignored; box, samples, seed, stream and p as for the built-in families).
- * Results (host array) as zmc_integrate's.  Blocking, on the context's stream. */
+ * desc[i].family must be ZMC_USER and desc[i].dim the udf's dimension, at most
+ * 7 here (deg is ignored; box, samples, seed, stream and p as for the built-in
+ * families; a udf of 8 to 12 dimensions integrates through
+ * zmc_normal_integrate_udf).  Results (host array) as zmc_integrate's.
+ * Blocking, on the context's stream. */
 zmc_status zmc_udf_integrate(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc *desc,
                              size_t n, zmc_result *out);
 
@@ -344,6 +346,59 @@ const char *zmc_udf_log(const zmc_udf *udf);
 
 /* Release a udf (NULL accepted).  Not while a call using it is running. */
 zmc_status zmc_udf_destroy(zmc_udf *udf);
+
+/* ---- Stratified sampling with a heuristic tree search (ZMCintegral_normal) -----
+ * The paper's normal mode (Sec. "Solution method", "Additional comments": for
+ * integrands of higher dimension, 8 to 12) stratifies the domain and refines
+ * the strata by a heuristic tree search; it gives no steps, and these calls
+ * implement this reading of it:
+ *   1. the box is cut into divisions^dim equal cells (cell j has grid index
+ *      (j / divisions^i) mod divisions in dimension i);
+ *   2. every cell is integrated by direct Monte Carlo with samples_per_cell
+ *      samples; the j-th cell created uses Philox stream stream_base + j and key
+ *      seed; e_c = V_c mean_c, s_c = V_c sqrt(M2_c / (N_c (N_c - 1)));
+ *   3. up to `depth` times: with tau = sigma_mult * (mean of s_c over the leaves),
+ *      every leaf with s_c > tau is split into its 2^dim halves (child b takes
+ *      the upper half of dimension i when bit i of b is set; mid = lo + (hi - lo)/2),
+ *      in leaf order while the leaf count stays <= max_leaves; the children take
+ *      their parent's place in the leaf order and are integrated as in step 2;
+ *      a round that splits nothing ends the search;
+ *   4. estimate = sum of e_c over the leaves, stderr = sqrt(sum of s_c^2).
+ * Cell boundaries: lo_i + ((hi_i - lo_i) * idx) / divisions, the last one hi_i. */
+typedef struct zmc_normal_opts {
+    uint32_t divisions;        /* cells per dimension at level 0 (>= 1; divisions^dim <= 2^20) */
+    uint32_t depth;            /* refinement rounds at most (0: plain stratified sampling)    */
+    uint64_t samples_per_cell; /* samples of every cell (2 .. 2^40)                           */
+    double sigma_mult;         /* split threshold factor (> 0)                                */
+    uint64_t seed;             /* Philox key of every cell                                    */
+    uint32_t stream_base;      /* stream of the first cell                                    */
+    uint32_t max_leaves;       /* cap on the leaf count (0: 2^20; at most 2^22)               */
+} zmc_normal_opts;
+
+typedef struct zmc_normal_result {
+    double estimate;
+    double stderr_;
+    uint64_t n_samples;        /* samples taken over every cell evaluated                     */
+    uint64_t n_cells;          /* cells evaluated (split ones included)                       */
+    uint64_t n_leaves;         /* cells of the final partition                                */
+    uint32_t rounds;           /* refinement rounds that split at least one leaf              */
+    int32_t status;
+} zmc_normal_result;
+
+/* divisions 2, depth 2, 2^14 samples per cell, sigma_mult 2, seed 0, stream 0,
+ * max_leaves 2^20. */
+zmc_status zmc_normal_default_options(zmc_normal_opts *opt);
+
+/* A built-in family integrand: base gives family, dim (<= 7), box and p; its
+ * n_samples, seed and stream_id are replaced by the options.  Blocking. */
+zmc_status zmc_normal_integrate(zmc_ctx *ctx, const zmc_desc *base, const zmc_normal_opts *opt,
+                                zmc_normal_result *out);
+
+/* A user-defined integrand of any dimension the udf was compiled for (1..12):
+ * lo, hi (udf dim values each) give the box, p the ZMC_NPARAM parameters. */
+zmc_status zmc_normal_integrate_udf(zmc_ctx *ctx, const zmc_udf *udf, const double *lo,
+                                    const double *hi, const double *p,
+                                    const zmc_normal_opts *opt, zmc_normal_result *out);
 
 /* ---- Integration without allocation (the paper has no counterpart) -------------
  * For callers that must not allocate device memory when they need a result: a

@@ -117,6 +117,20 @@ class Oracle:
                             x.reshape(-1), fx)
         return words, x, fx
 
+    def points(self, dim: int, lo, hi, seed: int, stream_id: int, s_begin: int, count: int):
+        """Sample points x (count, dim) of samples [s_begin, s_begin+count) of the
+        stream (seed, stream_id) on the box [lo, hi] of any dimension: the same
+        generator and map as ``samples``, without an integrand."""
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        assert len(lo) == len(hi) == dim
+        words = np.zeros((count, dim), dtype=np.uint32)
+        x = np.zeros((count, dim))
+        fx = np.zeros(count)
+        self.lib.zo_samples(4, int(dim), int(stream_id), 0, int(seed), lo, hi, np.zeros(40),
+                            int(s_begin), int(count), words.reshape(-1), x.reshape(-1), fx)
+        return x
+
 
 _lock = threading.Lock()
 _default = None
@@ -144,3 +158,7 @@ def moments(row, s_begin, s_end):
 
 def samples(row, s_begin, count):
     return default().samples(row, s_begin, count)
+
+
+def points(dim, lo, hi, seed, stream_id, s_begin, count):
+    return default().points(dim, lo, hi, seed, stream_id, s_begin, count)

@@ -102,6 +102,19 @@ void tune_cache_load(zmc_ctx *ctx);
 void tune_cache_store(zmc_ctx *ctx, const std::string &key, const TuneChoice &c);
 }  // namespace zmc
 
+// User-defined integrands (zmc_udf.cpp): one row of a udf integration; lo/hi
+// hold dim values, p ZMC_NPARAM.
+namespace zmc {
+struct UdfRow {
+  uint32_t dim = 0, stream_id = 0;
+  uint64_t n_samples = 0, seed = 0;
+  const double *lo = nullptr, *hi = nullptr, *p = nullptr;
+};
+zmc_status udf_run(zmc_ctx *ctx, const zmc_udf *udf, const UdfRow *rows, size_t n,
+                   zmc_result *out);
+uint32_t udf_dim(const zmc_udf *udf);
+}  // namespace zmc
+
 // Serving state (zmc_serving.cpp).
 struct ServingState;
 zmc_status serving_start(zmc_ctx *ctx);

@@ -26,6 +26,7 @@
 
 #include "zmc_jit_sources.h"
 #include "zmc_runtime.h"
+#include "zmc_udf_layout.h"
 
 using namespace zmc;
 
@@ -115,47 +116,42 @@ void put_f64(uint32_t *w, double v) { std::memcpy(w, &v, 8); }
 
 size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 
-// FnDev of one user descriptor (validated); p64 = device address of its FP64
-// parameters (ZMC_UDF_F64).
-zmc_status udf_fn(const zmc_udf *u, const zmc_desc &d, size_t i, uint64_t p64, FnDev *fn) {
-  if (d.family != ZMC_USER)
-    return set_error(ZMC_EINVAL, "descriptor %zu: family must be ZMC_USER", i);
+// FnDev of one user integrand (validated).  For ZMC_UDF_F64 the address of its
+// FP64 parameters is filled in by udf_run.
+zmc_status udf_fn(const zmc_udf *u, const UdfRow &d, size_t i, FnDev *fn) {
   if (d.dim != u->dim)
-    return set_error(ZMC_EINVAL, "descriptor %zu: dim %u, the udf was compiled for %u", i,
-                     d.dim, u->dim);
+    return set_error(ZMC_EINVAL, "row %zu: dim %u, the udf was compiled for %u", i, d.dim,
+                     u->dim);
   if (d.n_samples == 0 || d.n_samples > (1ull << 62))
-    return set_error(ZMC_EINVAL, "descriptor %zu: n_samples must be in 1..2^62", i);
+    return set_error(ZMC_EINVAL, "row %zu: n_samples must be in 1..2^62", i);
   std::memset(fn, 0, sizeof *fn);
   double vol = 1.0;
   const bool f32 = u->precision == ZMC_UDF_F32;
   for (uint32_t k = 0; k < d.dim; ++k) {
     if (!std::isfinite(d.lo[k]) || !std::isfinite(d.hi[k]) || !(d.lo[k] < d.hi[k]))
-      return set_error(ZMC_EINVAL, "descriptor %zu: box dimension %u needs finite lo < hi", i, k);
+      return set_error(ZMC_EINVAL, "row %zu: box dimension %u needs finite lo < hi", i, k);
     const double w = d.hi[k] - d.lo[k];
     vol *= w;
     if (f32) {
       if (!finite_f32(w) || !finite_f32(d.lo[k]))
-        return set_error(ZMC_EINVAL, "descriptor %zu: box out of FP32 range", i);
-      put_f32(&fn->w[k], w);
-      put_f32(&fn->w[7 + k], d.lo[k]);
+        return set_error(ZMC_EINVAL, "row %zu: box out of FP32 range", i);
+      put_f32(&fn->w[kUdfF32W + k], w);
+      put_f32(&fn->w[kUdfF32Lo + k], d.lo[k]);
     } else {
-      put_f64(&fn->w[2 * k], d.lo[k]);
-      put_f64(&fn->w[14 + 2 * k], w);
+      put_f64(&fn->w[kUdfF64Lo + 2 * k], d.lo[k]);
+      put_f64(&fn->w[kUdfF64W + 2 * k], w);
     }
   }
   for (int j = 0; j < ZMC_NPARAM; ++j) {
     if (!std::isfinite(d.p[j]) || (f32 && !finite_f32(d.p[j])))
-      return set_error(ZMC_EINVAL, "descriptor %zu: parameter p[%d] not finite%s", i, j,
+      return set_error(ZMC_EINVAL, "row %zu: parameter p[%d] not finite%s", i, j,
                        f32 ? " in FP32" : "");
-    if (f32) put_f32(&fn->w[14 + j], d.p[j]);
+    if (f32) put_f32(&fn->w[kUdfF32P + j], d.p[j]);
   }
-  if (f32) {
-    put_f32(&fn->w[54], u->scale);
-  } else {
-    fn->w[28] = static_cast<uint32_t>(p64);
-    fn->w[29] = static_cast<uint32_t>(p64 >> 32);
-    put_f64(&fn->w[30], u->scale);
-  }
+  if (f32)
+    put_f32(&fn->w[kUdfF32S], u->scale);
+  else
+    put_f64(&fn->w[kUdfF64S], u->scale);
   fn->variant = variant_code(ZMC_USER, d.dim, 0);
   fn->stream_id = d.stream_id;
   fn->key0 = static_cast<uint32_t>(d.seed);
@@ -164,6 +160,18 @@ zmc_status udf_fn(const zmc_udf *u, const zmc_desc &d, size_t i, uint64_t p64, F
   fn->volume = vol;
   fn->inv_scale = 1.0 / u->scale;  // a power of two: exact
   return ZMC_OK;
+}
+
+UdfRow row_of(const zmc_desc &d) {
+  UdfRow r;
+  r.dim = d.dim;
+  r.stream_id = d.stream_id;
+  r.n_samples = d.n_samples;
+  r.seed = d.seed;
+  r.lo = d.lo;
+  r.hi = d.hi;
+  r.p = d.p;
+  return r;
 }
 
 // Load the cubin (once per handle; the library is context independent).
@@ -206,7 +214,130 @@ struct ArenaBlocks {
   }
 };
 
+void set_param_address(FnDev *fn, const double *d_p) {
+  const uint64_t a = reinterpret_cast<uint64_t>(d_p);
+  fn->w[kUdfF64P] = static_cast<uint32_t>(a);
+  fn->w[kUdfF64P + 1] = static_cast<uint32_t>(a >> 32);
+}
+
 }  // namespace
+
+namespace zmc {
+
+// Integrate n user rows: the same FnDev / Entry / LaunchHdr tables as a plan,
+// the compiled persistent kernel, then the library's FP64 merge.  FP64
+// parameters are uploaded once per distinct parameter array.
+zmc_status udf_run(zmc_ctx *ctx, const zmc_udf *udf, const UdfRow *rows, size_t n,
+                   zmc_result *out) {
+  if (!ctx) return set_error(ZMC_EINVAL, "null context");
+  if (!udf || !rows || !out || n == 0) return set_error(ZMC_EINVAL, "bad udf arguments");
+  if (n >= (1u << 31)) return set_error(ZMC_EINVAL, "too many rows");
+  if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
+  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");
+  zmc_status st = udf_load(ctx, udf);
+  if (st != ZMC_OK) return st;
+
+  const bool f64 = udf->precision == ZMC_UDF_F64;
+  const uint64_t chunk = 128ull * ctx->quads_per_lane;
+  std::vector<FnDev> tab(n);
+  std::vector<uint64_t> rec_off(n);
+  std::vector<uint32_t> prow(n);        // FP64: index of the row's parameter block
+  std::vector<const double *> params;   // distinct parameter arrays, in first-use order
+  uint64_t total = 0;
+  for (size_t i = 0; i < n; ++i) {
+    st = udf_fn(udf, rows[i], i, &tab[i]);  // validates
+    if (st != ZMC_OK) return st;
+    rec_off[i] = total;
+    total += (rows[i].n_samples + chunk - 1) / chunk;
+    if (f64) {
+      if (params.empty() || params.back() != rows[i].p) {
+        if (params.size() >= (1u << 24)) return set_error(ZMC_EINVAL, "too many parameter rows");
+        params.push_back(rows[i].p);
+      }
+      prow[i] = static_cast<uint32_t>(params.size() - 1);
+    }
+  }
+  ArenaBlocks ab{ctx, {}};
+  const size_t fn_b = n * sizeof(FnDev), ent_b = n * sizeof(Entry), mrg_b = n * sizeof(FnDev *),
+               p_b = params.size() * ZMC_NPARAM * sizeof(double);
+  auto *d_fns = static_cast<FnDev *>(ab.get(fn_b));
+  auto *d_rec = static_cast<float2 *>(ab.get(total * sizeof(float2)));
+  auto *d_out = static_cast<zmc_result *>(ab.get(n * sizeof(zmc_result)));
+  auto *d_ent = static_cast<Entry *>(ab.get(ent_b));
+  auto *d_mrg = static_cast<const FnDev **>(ab.get(mrg_b));
+  auto *d_hdr = static_cast<LaunchHdr *>(ab.get(sizeof(LaunchHdr)));
+  auto *d_p = static_cast<double *>(p_b ? ab.get(p_b) : nullptr);
+  if (!d_fns || !d_rec || !d_out || !d_ent || !d_mrg || !d_hdr || (p_b && !d_p))
+    return set_error(ZMC_ENOMEM, "udf call needs %.1f MB of device memory",
+                     (fn_b + total * 8.0 + n * 64.0 + p_b) / 1e6);
+
+  // host tables in the pinned staging buffer: fns | entries | merge list | hdr | params
+  const size_t o_ent = round256(fn_b), o_mrg = o_ent + round256(ent_b),
+               o_hdr = o_mrg + round256(mrg_b), o_p = o_hdr + round256(sizeof(LaunchHdr)),
+               o_end = o_p + round256(p_b);
+  st = ensure_stage(ctx, std::max(o_end, n * sizeof(zmc_result)));
+  if (st != ZMC_OK) return st;
+  char *s = static_cast<char *>(ctx->stage);
+  auto *fns = reinterpret_cast<FnDev *>(s);
+  auto *ents = reinterpret_cast<Entry *>(s + o_ent);
+  auto *mrg = reinterpret_cast<const FnDev **>(s + o_mrg);
+  auto *hdr = reinterpret_cast<LaunchHdr *>(s + o_hdr);
+  auto *ps = reinterpret_cast<double *>(s + o_p);
+  for (size_t q = 0; q < params.size(); ++q)
+    std::memcpy(ps + q * ZMC_NPARAM, params[q], ZMC_NPARAM * sizeof(double));
+  uint64_t item = 0;
+  for (size_t i = 0; i < n; ++i) {
+    fns[i] = tab[i];
+    if (f64) set_param_address(&fns[i], d_p + static_cast<size_t>(prow[i]) * ZMC_NPARAM);
+    fns[i].rec = d_rec + rec_off[i];
+    fns[i].out = d_out + i;
+    ents[i].item_begin = item;
+    ents[i].fn = d_fns + i;
+    ents[i].chunk_begin = 0;
+    mrg[i] = d_fns + i;
+    item += (rows[i].n_samples + chunk - 1) / chunk;
+  }
+  std::memset(hdr, 0, sizeof *hdr);
+  hdr->item_end[0] = item;
+  hdr->n_entries = static_cast<uint32_t>(n);
+  hdr->n_merge = static_cast<uint32_t>(n);
+  hdr->quads_per_lane = ctx->quads_per_lane;
+
+  cudaStream_t str = ctx->stream;
+  e = cudaMemcpyAsync(d_fns, fns, fn_b, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ent, ents, ent_b, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_mrg, mrg, mrg_b, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_hdr, hdr, sizeof *hdr, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess && p_b) e = cudaMemcpyAsync(d_p, ps, p_b, cudaMemcpyHostToDevice, str);
+  if (e == cudaSuccess) {
+    // persistent grid: the kernel's occupancy, no more warps than work items
+    const uint64_t want = (item + 7) / 8;
+    const uint64_t cap = static_cast<uint64_t>(ctx->sms) * udf->max_blocks;
+    const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(want, cap)));
+    const Entry *a0 = d_ent;
+    LaunchHdr *a1 = d_hdr;
+    void *args[] = {&a0, &a1};
+    e = cudaLaunchKernel(reinterpret_cast<const void *>(udf->k_batched), dim3(grid), dim3(256),
+                         args, 0, str);
+  }
+  if (e == cudaSuccess) {
+    const unsigned mg = static_cast<unsigned>(
+        std::min<uint64_t>((n + 7) / 8, static_cast<uint64_t>(ctx->sms) * 16));
+    e = launch_merge(d_mrg, d_hdr, mg, str);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s, d_out, n * sizeof(zmc_result), cudaMemcpyDeviceToHost, str);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "udf integrate");
+  std::memcpy(out, s, n * sizeof(zmc_result));
+  return ZMC_OK;
+}
+
+uint32_t udf_dim(const zmc_udf *udf) { return udf ? udf->dim : 0; }
+
+}  // namespace zmc
 
 extern "C" {
 
@@ -214,7 +345,8 @@ zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
                           double amplitude, zmc_udf **out) {
   if (!source || !out) return set_error(ZMC_EINVAL, "null argument");
   *out = nullptr;
-  if (dim < 1 || dim > kMaxDim) return set_error(ZMC_EINVAL, "dim %u not in 1..7", dim);
+  if (dim < 1 || dim > static_cast<uint32_t>(kUdfMaxDim))
+    return set_error(ZMC_EINVAL, "dim %u not in 1..%d", dim, kUdfMaxDim);
   if (precision != ZMC_UDF_F32 && precision != ZMC_UDF_F64)
     return set_error(ZMC_EINVAL, "precision must be ZMC_UDF_F32 or ZMC_UDF_F64");
   if (!(amplitude >= 0.0) || !std::isfinite(amplitude))
@@ -227,10 +359,10 @@ zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
                      "#include \"zmc_device.cuh\"\n" + "#line 1 \"zmc_user_source\"\n" +
                      source + "\n#include \"zmc_udf_kernel.cuh\"\n";
   const char *hdr_text[] = {kJitZmcH,   kJitZmcInternalH, kJitZmcDeviceCuh, kJitZmcUdfKernelCuh,
-                            kStdint,    kCstdint,         kStddef,          kCstddef,
+                            kJitZmcUdfLayoutH, kStdint, kCstdint, kStddef, kCstddef,
                             kCudaRuntime};
   const char *hdr_name[] = {"zmc.h",    "zmc_internal.h", "zmc_device.cuh", "zmc_udf_kernel.cuh",
-                            "stdint.h", "cstdint",        "stddef.h",       "cstddef",
+                            "zmc_udf_layout.h", "stdint.h", "cstdint", "stddef.h", "cstddef",
                             "cuda_runtime.h"};
   const int n_hdr = static_cast<int>(sizeof hdr_name / sizeof hdr_name[0]);
   nvrtcProgram p = nullptr;
@@ -282,102 +414,16 @@ zmc_status zmc_udf_integrate(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc *d
                              zmc_result *out) {
   if (!ctx) return set_error(ZMC_EINVAL, "null context");
   if (!udf || !desc || !out || n == 0) return set_error(ZMC_EINVAL, "bad udf_integrate arguments");
-  if (n >= (1u << 31)) return set_error(ZMC_EINVAL, "too many descriptors");
-  if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
-  std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
-  cudaError_t e = cudaSetDevice(ctx->device);
-  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");
-  zmc_status st = udf_load(ctx, udf);
-  if (st != ZMC_OK) return st;
-
-  const bool f64 = udf->precision == ZMC_UDF_F64;
-  const uint64_t chunk = 128ull * ctx->quads_per_lane;
-  std::vector<FnDev> tab(n);
-  std::vector<uint64_t> rec_off(n);
-  uint64_t total = 0;
+  if (udf->dim > ZMC_MAX_DIM)
+    return set_error(ZMC_EINVAL, "a %u-dimensional udf takes boxes through zmc_normal_integrate_udf",
+                     udf->dim);
+  std::vector<UdfRow> rows(n);
   for (size_t i = 0; i < n; ++i) {
-    st = udf_fn(udf, desc[i], i, 0, &tab[i]);  // validates
-    if (st != ZMC_OK) return st;
-    rec_off[i] = total;
-    total += (desc[i].n_samples + chunk - 1) / chunk;
+    if (desc[i].family != ZMC_USER)
+      return set_error(ZMC_EINVAL, "descriptor %zu: family must be ZMC_USER", i);
+    rows[i] = row_of(desc[i]);
   }
-  ArenaBlocks ab{ctx, {}};
-  const size_t fn_b = n * sizeof(FnDev), ent_b = n * sizeof(Entry), mrg_b = n * sizeof(FnDev *),
-               p_b = f64 ? n * ZMC_NPARAM * sizeof(double) : 0;
-  auto *d_fns = static_cast<FnDev *>(ab.get(fn_b));
-  auto *d_rec = static_cast<float2 *>(ab.get(total * sizeof(float2)));
-  auto *d_out = static_cast<zmc_result *>(ab.get(n * sizeof(zmc_result)));
-  auto *d_ent = static_cast<Entry *>(ab.get(ent_b));
-  auto *d_mrg = static_cast<const FnDev **>(ab.get(mrg_b));
-  auto *d_hdr = static_cast<LaunchHdr *>(ab.get(sizeof(LaunchHdr)));
-  auto *d_p = static_cast<double *>(f64 ? ab.get(p_b) : nullptr);
-  if (!d_fns || !d_rec || !d_out || !d_ent || !d_mrg || !d_hdr || (f64 && !d_p))
-    return set_error(ZMC_ENOMEM, "udf call needs %.1f MB of device memory",
-                     (fn_b + total * 8.0 + n * 64.0 + p_b) / 1e6);
-
-  // host tables in the pinned staging buffer: fns | entries | merge list | hdr | params
-  const size_t o_ent = round256(fn_b), o_mrg = o_ent + round256(ent_b),
-               o_hdr = o_mrg + round256(mrg_b), o_p = o_hdr + round256(sizeof(LaunchHdr)),
-               o_end = o_p + round256(p_b);
-  st = ensure_stage(ctx, std::max(o_end, n * sizeof(zmc_result)));
-  if (st != ZMC_OK) return st;
-  char *s = static_cast<char *>(ctx->stage);
-  auto *fns = reinterpret_cast<FnDev *>(s);
-  auto *ents = reinterpret_cast<Entry *>(s + o_ent);
-  auto *mrg = reinterpret_cast<const FnDev **>(s + o_mrg);
-  auto *hdr = reinterpret_cast<LaunchHdr *>(s + o_hdr);
-  auto *ps = reinterpret_cast<double *>(s + o_p);
-  uint64_t item = 0;
-  for (size_t i = 0; i < n; ++i) {
-    fns[i] = tab[i];
-    if (f64) {
-      const uint64_t p64 = reinterpret_cast<uint64_t>(d_p + i * ZMC_NPARAM);
-      fns[i].w[28] = static_cast<uint32_t>(p64);
-      fns[i].w[29] = static_cast<uint32_t>(p64 >> 32);
-      std::memcpy(ps + i * ZMC_NPARAM, desc[i].p, ZMC_NPARAM * sizeof(double));
-    }
-    fns[i].rec = d_rec + rec_off[i];
-    fns[i].out = d_out + i;
-    ents[i].item_begin = item;
-    ents[i].fn = d_fns + i;
-    ents[i].chunk_begin = 0;
-    mrg[i] = d_fns + i;
-    item += (desc[i].n_samples + chunk - 1) / chunk;
-  }
-  std::memset(hdr, 0, sizeof *hdr);
-  hdr->item_end[0] = item;
-  hdr->n_entries = static_cast<uint32_t>(n);
-  hdr->n_merge = static_cast<uint32_t>(n);
-  hdr->quads_per_lane = ctx->quads_per_lane;
-
-  cudaStream_t str = ctx->stream;
-  e = cudaMemcpyAsync(d_fns, fns, fn_b, cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ent, ents, ent_b, cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_mrg, mrg, mrg_b, cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_hdr, hdr, sizeof *hdr, cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess && f64) e = cudaMemcpyAsync(d_p, ps, p_b, cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess) {
-    // persistent grid: the kernel's occupancy, no more warps than work items
-    const uint64_t want = (item + 7) / 8;
-    const uint64_t cap = static_cast<uint64_t>(ctx->sms) * udf->max_blocks;
-    const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(want, cap)));
-    const Entry *a0 = d_ent;
-    LaunchHdr *a1 = d_hdr;
-    void *args[] = {&a0, &a1};
-    e = cudaLaunchKernel(reinterpret_cast<const void *>(udf->k_batched), dim3(grid), dim3(256),
-                         args, 0, str);
-  }
-  if (e == cudaSuccess) {
-    const unsigned mg = static_cast<unsigned>(
-        std::min<uint64_t>((n + 7) / 8, static_cast<uint64_t>(ctx->sms) * 16));
-    e = launch_merge(d_mrg, d_hdr, mg, str);
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s, d_out, n * sizeof(zmc_result), cudaMemcpyDeviceToHost, str);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
-  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "udf integrate");
-  std::memcpy(out, s, n * sizeof(zmc_result));
-  return ZMC_OK;
+  return udf_run(ctx, udf, rows.data(), n, out);
 }
 
 zmc_status zmc_udf_eval_samples(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc *desc,
@@ -385,6 +431,7 @@ zmc_status zmc_udf_eval_samples(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc
   if (!ctx) return set_error(ZMC_EINVAL, "null context");
   if (!udf || !desc || !out) return set_error(ZMC_EINVAL, "null argument");
   if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
+  if (desc->family != ZMC_USER) return set_error(ZMC_EINVAL, "family must be ZMC_USER");
   if (count == 0) return ZMC_OK;
   if (s_begin + count > desc->n_samples)
     return set_error(ZMC_EINVAL, "sample range beyond n_samples");
@@ -404,8 +451,9 @@ zmc_status zmc_udf_eval_samples(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc
   if (st != ZMC_OK) return st;
   char *s = static_cast<char *>(ctx->stage);
   FnDev *fn = reinterpret_cast<FnDev *>(s);
-  st = udf_fn(udf, *desc, 0, f64 ? reinterpret_cast<uint64_t>(d_p) : 0, fn);
+  st = udf_fn(udf, row_of(*desc), 0, fn);
   if (st != ZMC_OK) return st;
+  if (f64) set_param_address(fn, d_p);
   std::memcpy(s + o_p, desc->p, ZMC_NPARAM * sizeof(double));
   cudaStream_t str = ctx->stream;
   e = cudaMemcpyAsync(d_fn, fn, sizeof(FnDev), cudaMemcpyHostToDevice, str);

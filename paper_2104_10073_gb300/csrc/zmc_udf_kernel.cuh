@@ -6,13 +6,10 @@
 // The generator, the per-chunk sums and the persistent work-list loop are those
 // of the built-in families (zmc_device.cuh); only the evaluation differs:
 // Eval<ZMC_USER, ZMC_UDF_DIM, 0> maps the sample onto the box and calls
-// zmc_user_f.  FnDev payload words (written by zmc_udf.cpp):
-//   ZMC_UDF_F32: fl32(hi_i - lo_i) at w[i], fl32(lo_i) at w[7+i],
-//                fl32(p_j) at w[14+j] (j < 40), S at w[54];
-//   ZMC_UDF_F64: lo_i at w[2i], hi_i - lo_i at w[14+2i] (FP64, two words each),
-//                the device address of the integrand's 40 FP64 parameters at
-//                w[28], S (FP64) at w[30].
-// The kernels have C names so that the loader can find them.
+// zmc_user_f; the FnDev payload words it reads are laid out in zmc_udf_layout.h
+// (written by zmc_udf.cpp).  The kernels have C names so that the loader can
+// find them.
+#include "zmc_udf_layout.h"
 
 namespace zmc {
 namespace {
@@ -26,12 +23,12 @@ struct Eval<ZMC_USER, D, G> {
   __device__ __forceinline__ void load(const FnDev *fn) {
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      wd[i] = __uint_as_float(fn->w[i]);
-      lo[i] = __uint_as_float(fn->w[7 + i]);
+      wd[i] = __uint_as_float(fn->w[kUdfF32W + i]);
+      lo[i] = __uint_as_float(fn->w[kUdfF32Lo + i]);
     }
 #pragma unroll
-    for (int j = 0; j < ZMC_NPARAM; ++j) p[j] = __uint_as_float(fn->w[14 + j]);
-    S = __uint_as_float(fn->w[54]);
+    for (int j = 0; j < ZMC_NPARAM; ++j) p[j] = __uint_as_float(fn->w[kUdfF32P + j]);
+    S = __uint_as_float(fn->w[kUdfF32S]);
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
     float x[D];
@@ -53,13 +50,13 @@ struct Eval<ZMC_USER, D, G> {
   __device__ __forceinline__ void load(const FnDev *fn) {
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      lo[i] = word_pair_f64(fn->w + 2 * i);
-      wd[i] = word_pair_f64(fn->w + 14 + 2 * i);
+      lo[i] = word_pair_f64(fn->w + kUdfF64Lo + 2 * i);
+      wd[i] = word_pair_f64(fn->w + kUdfF64W + 2 * i);
     }
     const unsigned long long addr =
-        (static_cast<unsigned long long>(fn->w[29]) << 32) | fn->w[28];
+        (static_cast<unsigned long long>(fn->w[kUdfF64P + 1]) << 32) | fn->w[kUdfF64P];
     p = reinterpret_cast<const double *>(addr);
-    S = word_pair_f64(fn->w + 30);
+    S = word_pair_f64(fn->w + kUdfF64S);
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
     double x[D];

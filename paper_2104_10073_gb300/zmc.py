@@ -55,6 +55,20 @@ class zmc_plan_info(ctypes.Structure):
                 ("family_block", ctypes.c_uint32 * 4), ("tune_source", ctypes.c_int32 * 4)]
 
 
+class zmc_normal_opts(ctypes.Structure):
+    _fields_ = [("divisions", ctypes.c_uint32), ("depth", ctypes.c_uint32),
+                ("samples_per_cell", ctypes.c_uint64), ("sigma_mult", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("stream_base", ctypes.c_uint32),
+                ("max_leaves", ctypes.c_uint32)]
+
+
+class zmc_normal_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("stderr_", ctypes.c_double),
+                ("n_samples", ctypes.c_uint64), ("n_cells", ctypes.c_uint64),
+                ("n_leaves", ctypes.c_uint64), ("rounds", ctypes.c_uint32),
+                ("status", ctypes.c_int32)]
+
+
 class zmc_serving_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "completed", "cancelled", "queued", "running", "iterations",
@@ -104,6 +118,11 @@ _SIGS = {
     "zmc_udf_eval_samples": ([_P, _P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_udf_log": ([_P], ctypes.c_char_p),
     "zmc_udf_destroy": ([_P], ctypes.c_int),
+    "zmc_normal_default_options": ([ctypes.POINTER(zmc_normal_opts)], ctypes.c_int),
+    "zmc_normal_integrate": ([_P, _P, ctypes.POINTER(zmc_normal_opts),
+                              ctypes.POINTER(zmc_normal_result)], ctypes.c_int),
+    "zmc_normal_integrate_udf": ([_P, _P, _P, _P, _P, ctypes.POINTER(zmc_normal_opts),
+                                  ctypes.POINTER(zmc_normal_result)], ctypes.c_int),
     "zmc_desc_size": ([], ctypes.c_size_t),
     "zmc_result_size": ([], ctypes.c_size_t),
 }
@@ -355,6 +374,31 @@ def zmc_validate(desc):
 
 
 # ------------------------------------------------------------------ convenience
+def normal_options(**kw) -> zmc_normal_opts:
+    """zmc_normal_opts with the library defaults, overridden by keyword."""
+    o = zmc_normal_opts()
+    _check(lib().zmc_normal_default_options(ctypes.byref(o)), "zmc_normal_default_options")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _normal_dict(r: zmc_normal_result) -> dict:
+    return {"estimate": r.estimate, "stderr": r.stderr_, "n_samples": r.n_samples,
+            "n_cells": r.n_cells, "n_leaves": r.n_leaves, "rounds": r.rounds}
+
+
+def zmc_normal_integrate(ctx: int, base_row, opts: zmc_normal_opts) -> dict:
+    """Stratified sampling with tree refinement of one built-in integrand."""
+    t = _table(np.asarray(base_row).reshape(1))
+    r = zmc_normal_result()
+    _check(lib().zmc_normal_integrate(ctx, t.ctypes.data, ctypes.byref(opts), ctypes.byref(r)),
+           "zmc_normal_integrate")
+    return _normal_dict(r)
+
+
 class Udf:
     """A user-defined integrand compiled at run time (NVRTC); see zmc_udf_create.
 
@@ -387,6 +431,20 @@ class Udf:
         _check(lib().zmc_udf_eval_samples(ctx, self.handle, t.ctypes.data, s_begin, count,
                                           out.ctypes.data), "zmc_udf_eval_samples")
         return out
+
+    def normal_integrate(self, ctx: int, lo, hi, p, opts: zmc_normal_opts) -> dict:
+        """Stratified sampling with tree refinement over the box [lo, hi]."""
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        pp = np.zeros(40)
+        pv = np.asarray(p, dtype=np.float64).reshape(-1)
+        pp[:len(pv)] = pv
+        assert len(lo) == len(hi) == self.dim
+        r = zmc_normal_result()
+        _check(lib().zmc_normal_integrate_udf(ctx, self.handle, lo.ctypes.data, hi.ctypes.data,
+                                              pp.ctypes.data, ctypes.byref(opts),
+                                              ctypes.byref(r)), "zmc_normal_integrate_udf")
+        return _normal_dict(r)
 
     def close(self):
         if self.handle:

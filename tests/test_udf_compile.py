@@ -41,7 +41,7 @@ __device__ double zmc_user_f(const double *x, const double *p) {
 """
 
 
-@pytest.mark.parametrize("dim", [1, 4, 7])
+@pytest.mark.parametrize("dim", [1, 4, 7, 12])
 def test_compiles_for_both_precisions(dim):
     a = zmc.Udf(F32_SRC, dim, zmc.ZMC_UDF_F32)
     b = zmc.Udf(F64_SRC, dim, zmc.ZMC_UDF_F64, amplitude=10.0)
@@ -72,7 +72,7 @@ def test_wrong_precision_signature_is_reported():
     assert e.value.status == zmc.ZMC_EINVAL
 
 
-@pytest.mark.parametrize("dim,prec,amp", [(0, 0, 0.0), (8, 0, 0.0), (2, 2, 0.0), (2, 0, -1.0),
+@pytest.mark.parametrize("dim,prec,amp", [(0, 0, 0.0), (13, 0, 0.0), (2, 2, 0.0), (2, 0, -1.0),
                                           (2, 0, float("inf"))])
 def test_arguments_are_validated(dim, prec, amp):
     with pytest.raises(zmc.ZmcError) as e:
