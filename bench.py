@@ -270,7 +270,7 @@ def run_native(args, world, rank, local):
 
     tune_path = os.path.join(tempfile.gettempdir(), f"zmc_tune_{os.getuid()}_{local}.json")
     ctx = zmc.Context(arena_bytes=2 << 30, device=local, autotune=not args.no_autotune,
-                      tune_cache_path=tune_path)
+                      tune_cache_path=tune_path, quads_per_lane=args.quads_per_lane)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     tab = fig1_table(rank)
     n_samples = W.total_samples(tab)
@@ -613,6 +613,8 @@ def main():
                          "stratified (normal-mode) legs")
     ap.add_argument("--cpu-repeats", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--quads-per-lane", type=int, default=16,
+                    help="chunk length = 128 x this many samples")
     ap.add_argument("--serving-sweep", action="store_true")
     ap.add_argument("--serving-rates", type=float, nargs="+",
                     default=[10.0, 30.0, 100.0, 300.0, 1000.0])

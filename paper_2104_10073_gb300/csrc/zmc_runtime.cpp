@@ -470,10 +470,18 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
   std::vector<uint64_t> len(n);
   plan->plain.resize(n);
   plan->volume.resize(n);
+  // per-descriptor validation and FP64 precompute, in parallel for large tables;
+  // the first failing row is redone on this thread for its message
+  std::vector<uint8_t> ok(n, 1);
+  host_parallel_for(n, 64, [&](size_t b, size_t e) {
+    for (size_t i = b; i < e; ++i)
+      ok[i] = precompute(desc[i], &fns[i], &plan->plain[i], &plan->volume[i]) == ZMC_OK;
+  });
   for (size_t i = 0; i < n; ++i) {
-    zmc_status st = precompute(desc[i], &fns[i], &plan->plain[i], &plan->volume[i]);
-    if (st != ZMC_OK)
+    if (!ok[i]) {
+      const zmc_status st = precompute(desc[i], &fns[i], &plan->plain[i], &plan->volume[i]);
       return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    }
     len[i] = desc[i].n_samples;
     if (s_begin) {
       if (s_begin[i] % 4 != 0 || !(s_end[i] > s_begin[i]) || s_end[i] - s_begin[i] > (1ull << 62))
@@ -716,13 +724,17 @@ size_t zmc_desc_size(void) { return sizeof(zmc_desc); }
 
 zmc_status zmc_validate(const zmc_desc *desc, size_t n, size_t *bad_index) {
   if (!desc && n) return set_error(ZMC_EINVAL, "null descriptor table");
-  FnDev fn;
+  std::vector<uint8_t> ok(n, 1);
+  host_parallel_for(n, 64, [&](size_t b, size_t e) {
+    FnDev fn;
+    for (size_t i = b; i < e; ++i) ok[i] = precompute(desc[i], &fn, nullptr, nullptr) == ZMC_OK;
+  });
   for (size_t i = 0; i < n; ++i) {
-    zmc_status st = precompute(desc[i], &fn, nullptr, nullptr);
-    if (st != ZMC_OK) {
-      if (bad_index) *bad_index = i;
-      return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
-    }
+    if (ok[i]) continue;
+    FnDev fn;
+    const zmc_status st = precompute(desc[i], &fn, nullptr, nullptr);
+    if (bad_index) *bad_index = i;
+    return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
   }
   return ZMC_OK;
 }

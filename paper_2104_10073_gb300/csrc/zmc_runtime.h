@@ -102,6 +102,14 @@ void tune_cache_load(zmc_ctx *ctx);
 void tune_cache_store(zmc_ctx *ctx, const std::string &key, const TuneChoice &c);
 }  // namespace zmc
 
+// Host thread pool (zmc_pool.cpp): fn(begin, end) over [0, n) in ranges of
+// `grain`, on the calling thread and the pool's workers; returns when all ranges
+// are done.  Small n runs inline.
+#include <functional>
+namespace zmc {
+void host_parallel_for(size_t n, size_t grain, const std::function<void(size_t, size_t)> &fn);
+}  // namespace zmc
+
 // User-defined integrands (zmc_udf.cpp): one row of a udf integration; lo/hi
 // hold dim values, p ZMC_NPARAM.
 namespace zmc {

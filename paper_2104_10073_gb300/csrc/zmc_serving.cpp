@@ -602,9 +602,15 @@ zmc_status submit_job(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *fro
   j->nchunk.resize(n);
   j->next_chunk.assign(n, 0);
   const uint64_t chunk = 128ull * ctx->quads_per_lane;
+  std::vector<uint8_t> ok(n, 1);
+  host_parallel_for(n, 64, [&](size_t b, size_t e) {
+    for (size_t i = b; i < e; ++i) ok[i] = precompute(desc[i], &j->fns[i], nullptr, nullptr) == ZMC_OK;
+  });
   for (size_t i = 0; i < n; ++i) {
-    zmc_status st = precompute(desc[i], &j->fns[i], nullptr, nullptr);
-    if (st != ZMC_OK) return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    if (!ok[i]) {
+      const zmc_status st = precompute(desc[i], &j->fns[i], nullptr, nullptr);
+      return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    }
     uint64_t start = 0;
     if (from && from[i].n > 0) {
       const zmc_moments &m = from[i];

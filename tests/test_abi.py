@@ -101,3 +101,19 @@ def test_create_without_gpu_fails_cleanly(lib):
     with pytest.raises(zmc.ZmcError) as e:
         zmc.zmc_create()
     assert e.value.status == zmc.ZMC_ECUDA
+
+
+def test_validation_reports_the_first_bad_row_of_a_large_table(lib):
+    """Large tables are validated on several host threads; the reported row is
+    still the first bad one, with its own message."""
+    t = W.mixed(6000, gen_seed=3)
+    t["dim"][4500] = 9
+    t["n_samples"][3777] = 0
+    t["lo"][5000][0] = t["hi"][5000][0]
+    for _ in range(5):
+        st, bad, msg = zmc.zmc_validate(t)
+        assert st == zmc.ZMC_EINVAL and bad == 3777
+        assert "3777" in msg and "n_samples" in msg
+    t["n_samples"][3777] = 10
+    st, bad, msg = zmc.zmc_validate(t)
+    assert st == zmc.ZMC_EINVAL and bad == 4500 and "dim" in msg
