@@ -613,7 +613,7 @@ def main():
                          "stratified (normal-mode) legs")
     ap.add_argument("--cpu-repeats", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--quads-per-lane", type=int, default=16,
+    ap.add_argument("--quads-per-lane", type=int, default=64,
                     help="chunk length = 128 x this many samples")
     ap.add_argument("--serving-sweep", action="store_true")
     ap.add_argument("--serving-rates", type=float, nargs="+",

@@ -116,7 +116,7 @@ typedef struct zmc_options {
                                     on a slice of a new plan's work (or reuse the
                                     cache); never changes results                   */
     int32_t device;              /* CUDA device ordinal                              */
-    uint32_t quads_per_lane;     /* chunk = 128 * quads_per_lane samples; 0 -> 16.
+    uint32_t quads_per_lane;     /* chunk = 128 * quads_per_lane samples; 0 -> 64.
                                     Results are bit-identical for a fixed value and
                                     agree within rounding across values.            */
     const char *tune_cache_path; /* autotune JSON cache; NULL -> no file             */
@@ -416,14 +416,14 @@ zmc_status zmc_normal_integrate_udf(zmc_ctx *ctx, const zmc_udf *udf, const doub
  * ZMC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.
  *   - At most ZMC_NOALLOC_MAX_FNS integrands (ZMC_EINVAL beyond) and at most
- *     ~4e9 samples in total at 2048 samples per chunk (ZMC_ENOMEM beyond, with
+ *     ~1.6e10 samples in total at 8192 samples per chunk (ZMC_ENOMEM beyond, with
  *     the needed size in zmc_last_error()).
  *   - All calls share the array and it keeps the previous call's contents; each
  *     call re-uploads its tables and zeroes its work counters.  Calls whose GPU
  *     work overlaps (other streams, or unordered host threads) race: order them.
  *   - The first call on a device looks up the array's device address with that
  *     device current; make it before any stream capture.
- *   - Results equal zmc_integrate's with the default quads_per_lane (16).      */
+ *   - Results equal zmc_integrate's with the default quads_per_lane (64).      */
 #define ZMC_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define ZMC_NOALLOC_MAX_FNS 4096u
 zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_result *out,

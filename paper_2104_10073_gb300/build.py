@@ -24,7 +24,8 @@ BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["zmc_fam_harmonic.cu", "zmc_fam_abslin.cu", "zmc_fam_gauss.cu", "zmc_fam_poly.cu",
            "zmc_plain.cu", "zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp",
-           "zmc_noalloc.cu", "zmc_tune.cpp", "zmc_udf.cpp", "zmc_normal.cpp", "zmc_pool.cpp"]
+           "zmc_noalloc.cu", "zmc_tune.cpp", "zmc_udf.cpp", "zmc_normal.cpp", "zmc_pool.cpp",
+           "zmc_polyroots.cpp"]
 HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h", "zmc_device.cuh",
            "zmc_udf_kernel.cuh", "zmc_udf_layout.h"]
 # Headers whose text zmc_udf.cpp hands to NVRTC (symbol name, path).

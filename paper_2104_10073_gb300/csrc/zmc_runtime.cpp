@@ -125,6 +125,68 @@ double binom(int n, int k) {
 }
 }  // namespace
 
+// Product polynomial of degree g >= 2 in root form (variant degree g + 3).  Each
+// factor is lead * (its roots grouped into "quads" and, for g = 3, one linear
+// term): a quad is (u - p1)(u - p2) + c, either a pair of real roots (p1, p2,
+// c = 0) or a complex pair a +- ib (p1 = p2 = a, c = b^2); the linear term is
+// u - r.  Words per dimension i: g = 2: quad (p1 hi, p1 lo, p2 hi, p2 lo, c) at
+// w[5i..]; g = 3: linear (r hi, r lo) then quad at w[7i..]; g = 4: two quads at
+// w[10i..]; the amplitude S prod_i lead_i at w[70].  False (keep the
+// coefficient form) when a factor has no reliable root form or a lower degree
+// than g, a leading coefficient below 1e-6 of its factor's coefficient sum, or
+// a root beyond 2^10 in size.
+static bool poly_roots_payload(const double (*e)[5], int dim, int g, double S, FnDev *fn) {
+  const int words = g == 2 ? 5 : g == 3 ? 7 : 10;
+  double amp = S;
+  uint32_t w[kMaxDim * 10];
+  for (int i = 0; i < dim; ++i) {
+    RootForm rf;
+    if (!poly_root_form(e[i], g, &rf) || rf.n != g) return false;
+    double sum = 0.0;
+    for (int k = 0; k <= g; ++k) sum += std::fabs(e[i][k]);
+    if (!(std::fabs(rf.lead) >= 1e-6 * sum)) return false;
+    double reals[4], ca[2], cb2[2];
+    int nr = 0, nc = 0;
+    for (int s = 0; s < rf.n; ++s) {
+      if (!(std::fabs(rf.v[s]) <= 1024.0)) return false;
+      if (rf.type[s] == 1) reals[nr++] = rf.v[s];
+      if (rf.type[s] == 2) {
+        ca[nc] = rf.v[s];
+        cb2[nc++] = rf.v[s + 1];
+      }
+    }
+    uint32_t *o = w + words * i;
+    auto quad = [&](uint32_t *q, double p1, double p2, double c) {
+      split(p1, &q[0], &q[1]);
+      split(p2, &q[2], &q[3]);
+      put_f32(&q[4], c);
+    };
+    int ri = 0, ci = 0;
+    if (g == 3) {  // the linear term takes a real root (a cubic has at least one)
+      split(reals[ri], &o[0], &o[1]);
+      ++ri;
+      o += 2;
+    }
+    for (int qd = 0; qd < (g == 3 ? 1 : g / 2); ++qd, o += 5) {
+      if (ci < nc) {
+        quad(o, ca[ci], ca[ci], cb2[ci]);
+        ++ci;
+      } else if (ri + 1 < nr) {
+        quad(o, reals[ri], reals[ri + 1], 0.0);
+        ri += 2;
+      } else {
+        return false;
+      }
+    }
+    amp *= rf.lead;
+  }
+  if (!finite_f32(amp)) return false;
+  std::memcpy(fn->w, w, sizeof(uint32_t) * words * dim);
+  put_f32(&fn->w[70], amp);
+  fn->variant = variant_code(ZMC_POLY, static_cast<uint32_t>(dim), static_cast<uint32_t>(g + 3));
+  return true;
+}
+
 zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volume) {
   if (d.family > ZMC_POLY) return set_error(ZMC_EINVAL, "unknown family %u", d.family);
   if (d.dim < 1 || d.dim > kMaxDim) return set_error(ZMC_EINVAL, "dim %u not in 1..7", d.dim);
@@ -275,6 +337,7 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
     }
     default: {
       const int g = static_cast<int>(d.deg);
+      if (g >= 2 && poly_roots_payload(poly_e, dim, g, S, fn)) break;
       for (int i = 0; i < dim; ++i) {
         for (int k = 0; k <= g; ++k) {
           const double e = (i == 0 ? S : 1.0) * poly_e[i][k];
@@ -714,7 +777,7 @@ zmc_status zmc_default_options(zmc_options *opt) {
   if (!opt) return set_error(ZMC_EINVAL, "null options");
   std::memset(opt, 0, sizeof *opt);
   opt->mem_budget_bytes = 1ull << 30;
-  opt->quads_per_lane = 16;
+  opt->quads_per_lane = 64;
   return ZMC_OK;
 }
 
@@ -747,7 +810,7 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   zmc_default_options(&opt);
   if (opt_in) opt = *opt_in;
   if (opt.mem_budget_bytes == 0) opt.mem_budget_bytes = 1ull << 30;
-  if (opt.quads_per_lane == 0) opt.quads_per_lane = 16;
+  if (opt.quads_per_lane == 0) opt.quads_per_lane = 64;
   if (opt.quads_per_lane > 1024) return set_error(ZMC_EINVAL, "quads_per_lane above 1024");
   if (opt.arena && (reinterpret_cast<uintptr_t>(opt.arena) & 255))
     return set_error(ZMC_EINVAL, "arena must be 256-byte aligned");

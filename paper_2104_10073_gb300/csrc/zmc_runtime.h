@@ -102,6 +102,21 @@ void tune_cache_load(zmc_ctx *ctx);
 void tune_cache_store(zmc_ctx *ctx, const std::string &key, const TuneChoice &c);
 }  // namespace zmc
 
+// Root form of a real polynomial sum_k e[k] u^k of degree <= 4 (zmc_polyroots.cpp):
+//   q(u) = lead * prod_s f_s(u); slot s of type 1 is a real root, f_s = u - v[s];
+//   type 2 opens a complex pair, f_s = (u - v[s])^2 + v[s+1] (v[s+1] > 0), and
+//   the pair's second slot has type 3.  False when no reliable form was found
+//   (the caller then keeps the coefficients).
+namespace zmc {
+struct RootForm {
+  double lead;
+  int n;            // slots used
+  uint8_t type[4];
+  double v[4];
+};
+bool poly_root_form(const double *e, int g, RootForm *out);
+}  // namespace zmc
+
 // Host thread pool (zmc_pool.cpp): fn(begin, end) over [0, n) in ranges of
 // `grain`, on the calling thread and the pool's workers; returns when all ranges
 // are done.  Small n runs inline.

@@ -523,7 +523,11 @@ void scheduler_loop(ServingState *S) {
 zmc_status serving_start(zmc_ctx *ctx) {
   auto S = std::make_unique<ServingState>();
   S->ctx = ctx;
-  S->max_chunks = ctx->max_chunks_per_iter ? ctx->max_chunks_per_iter : (1u << 18);
+  // default: ~5.4e8 samples per iteration (about 1.8 ms of sampling) whatever the
+  // chunk length
+  S->max_chunks = ctx->max_chunks_per_iter
+                      ? ctx->max_chunks_per_iter
+                      : std::max<uint32_t>(1024, (1u << 22) / ctx->quads_per_lane);
   S->max_entries = std::max<uint32_t>(S->max_chunks, 1024);
   S->max_entries = std::min<uint32_t>(S->max_entries, 1u << 20);
   S->max_merge = 1u << 16;

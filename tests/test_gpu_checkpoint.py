@@ -17,7 +17,7 @@ from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
 
-CHUNK = 128 * 16  # samples per chunk at the default quads_per_lane
+CHUNK = 128 * zmc.DEFAULT_QUADS_PER_LANE  # samples per chunk at the default
 
 
 @pytest.fixture(scope="module")

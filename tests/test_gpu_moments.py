@@ -17,7 +17,7 @@ from paper_2104_10073_gb300 import zmc
 from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
-CHUNK = 2048
+CHUNK = 128 * zmc.DEFAULT_QUADS_PER_LANE  # samples per chunk at the default
 
 
 def _volumes(t):

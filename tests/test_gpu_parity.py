@@ -1,7 +1,7 @@
 """CUDA path (through the C ABI) against the FP64 oracle on identical samples.
 
 Tolerances are stated in tests/gpu_common.py.  Sizes span many chunks and
-ragged tails (chunk = 128 * quads_per_lane = 2048 samples by default); the
+ragged tails (chunk = 128 * quads_per_lane = 8192 samples by default); the
 full-size mixed table runs in the benchmark's launch configuration and is
 checked on sampled rows the oracle computes one by one.
 """
@@ -18,8 +18,8 @@ from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
 
-EDGE_SIZES = [1, 2, 3, 4, 5, 7, 8, 127, 128, 129, 2047, 2048, 2049, 4095, 4096, 4097, 10003,
-              65537]
+EDGE_SIZES = [1, 2, 3, 4, 5, 7, 8, 127, 128, 129, 2047, 2048, 2049, 4095, 4096, 4097, 8191,
+              8192, 8193, 10003, 16385, 65537]
 
 
 # ------------------------------------------------------------------ generator
@@ -73,6 +73,38 @@ def test_eval_samples_match_oracle_per_sample(zctx):
             tol = 4e-6 * G.sample_scale(row)
             err = np.max(np.abs(got - want))
             assert err <= tol, (int(row["family"]), int(row["dim"]), s0, err, tol)
+
+
+def test_poly_relative_accuracy_near_roots(zctx):
+    """Product polynomials whose factors have roots inside the box: every
+    sample's value keeps its relative accuracy, even where a factor nearly
+    vanishes (the root form; Horner on the coefficients loses up to the ratio of
+    the summed terms to the value there).  Factors are built from given roots so
+    that several lie inside [lo, hi]."""
+    rng = np.random.default_rng(77)
+    for d, deg in ((1, 2), (2, 4), (3, 3), (5, 4), (7, 2), (7, 4)):
+        t = W.empty(1)
+        lo = rng.uniform(-1.0, 0.0, d)
+        hi = lo + rng.uniform(0.5, 2.0, d)
+        coef = np.zeros((d, deg + 1))
+        for i in range(d):
+            roots = list(rng.uniform(lo[i], hi[i], deg))
+            if deg >= 2 and rng.random() < 0.5:  # a complex pair near the box
+                a, b = rng.uniform(lo[i], hi[i]), rng.uniform(0.01, 0.3)
+                roots[:2] = [a + 1j * b, a - 1j * b]
+            c = np.array([rng.uniform(0.5, 2.0)], dtype=complex)
+            for r in roots:
+                c = np.convolve(c, [-r, 1.0])
+            coef[i] = np.real(c)
+        W.poly(t[0], coef, lo, hi, 10**6, seed=d, stream_id=deg)
+        got = zmc.zmc_eval_samples(zctx.handle, t[0], 1000, 4000).astype(np.float64)
+        _, _, want = oracle.samples(t[0], 1000, 4000)
+        rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-30)
+        # FP32: a few ulp per factor and per product; values within 1e-5 of a
+        # root in relative terms are left to the absolute check
+        ok = rel <= 2e-6
+        assert np.mean(ok) >= 0.999, (d, deg, np.sort(rel)[-5:])
+        assert np.max(np.abs(got - want)) <= 2e-6 * G.sample_scale(t[0]), (d, deg)
 
 
 def test_eval_samples_across_block_index_carry(zctx):

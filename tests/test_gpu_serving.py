@@ -108,18 +108,21 @@ def test_job_larger_than_budget_is_refused():
 
 def test_admission_waits_for_memory():
     """Jobs that do not all fit at once are admitted as earlier ones finish."""
-    with zmc.Context(arena_bytes=96 << 20, serving=True, max_chunks_per_iter=65536) as c:
+    with zmc.Context(arena_bytes=12 << 20, serving=True, max_chunks_per_iter=4096) as c:
+        chunk = 128 * zmc.DEFAULT_QUADS_PER_LANE
+        n = 2**31 // chunk * chunk  # 2^31 samples: 2 MiB of chunk records per job
         jobs = []
-        for j in range(6):
+        for j in range(12):
             t = W.empty(1)
-            # ~2.4e4 chunks x 8 B records + tables: several jobs exceed the arena together
-            W.harmonic(t[0], 1.0, 0.5, [3.0, 1.0], [0.0, 0.0], [1.0, 1.0], 5 * 10**7, seed=j)
+            W.harmonic(t[0], 1.0, 0.5, [3.0, 1.0], [0.0, 0.0], [1.0, 1.0], n, seed=j)
             jobs.append(t)
         ids = [zmc.zmc_submit(c.handle, t) for t in jobs]
-        res = [zmc.zmc_poll(c.handle, i, 1, wait_ms=-1) for i in ids]
+        stats = zmc.zmc_serving_stats_get(c.handle)
+        assert stats["queued"] >= 1  # 12 x 2 MiB cannot all be admitted into 12 MiB
+        res = [zmc.zmc_poll(c.handle, i, 1, wait_ms=120000) for i in ids]
         assert all(st == zmc.ZMC_OK for st, _ in res)
         stats = zmc.zmc_serving_stats_get(c.handle)
-        assert stats["completed"] >= 6
+        assert stats["completed"] >= 12
 
 
 def test_poisson_stream_latency_recorded(sctx):
