@@ -411,12 +411,13 @@ def run_native(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(zmc, device, rate_hz, seconds):
+def run_serving(zmc, device, rate_hz, seconds, quads_per_lane=0):
     """Poisson job stream through zmc_submit; a collector thread takes finished
     ids from zmc_poll_any and the results from zmc_poll.  Latency = submit call
     to results collected."""
     jobs = W.serving_stream(rate_hz, seconds, max_fns=1000)
-    ctx = zmc.Context(arena_bytes=8 << 30, device=device, serving=True)
+    ctx = zmc.Context(arena_bytes=8 << 30, device=device, serving=True,
+                      quads_per_lane=quads_per_lane)
     submitted = {}
     done = {}
     lock = threading.Lock()
@@ -589,7 +590,7 @@ def run_serving_sweep(args):
     build.build()
     out = []
     for rate in args.serving_rates:
-        r = run_serving(zmc, 0, rate, args.serving_seconds)
+        r = run_serving(zmc, 0, rate, args.serving_seconds, args.serving_quads)
         if r is not None:
             r["demand_gsps"] = rate * 500.5 * 1.444e6 / 1e9  # E[jobs/s x rows x N]
         out.append(r)
@@ -621,6 +622,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=100.0)
     ap.add_argument("--serving-seconds", type=float, default=10.0)
+    ap.add_argument("--serving-quads", type=int, default=0,
+                    help="chunk length of the serving context (0: library default)")
     args = ap.parse_args()
     world, rank, local = (int(os.environ.get("WORLD_SIZE", "1")),
                           int(os.environ.get("RANK", "0")),

@@ -116,7 +116,8 @@ typedef struct zmc_options {
                                     on a slice of a new plan's work (or reuse the
                                     cache); never changes results                   */
     int32_t device;              /* CUDA device ordinal                              */
-    uint32_t quads_per_lane;     /* chunk = 128 * quads_per_lane samples; 0 -> 64.
+    uint32_t quads_per_lane;     /* chunk = 128 * quads_per_lane samples; 0 -> 64,
+                                    or 32 when serving is set.
                                     Results are bit-identical for a fixed value and
                                     agree within rounding across values.            */
     const char *tune_cache_path; /* autotune JSON cache; NULL -> no file             */

@@ -64,12 +64,33 @@ struct Job;
 
 struct zmc_plan;
 
+namespace zmc {
+// Side streams and events that run the family kernels of one launch
+// concurrently: forked from a main stream and joined back into it (also inside
+// a stream capture, where the fork and join become graph edges).  A family
+// kernel's blocks then fill the SMs that the previous family's last chunks
+// leave idle, instead of waiting for its tail.
+struct FamilyFork {
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[3] = {nullptr, nullptr, nullptr};
+  cudaError_t init();
+  void destroy();
+};
+// Launch the batched kernels of the families with present[f] on `main`,
+// concurrently when more than one is present.
+cudaError_t launch_families(FamilyFork &ff, const Entry *entries, LaunchHdr *hdr,
+                            const unsigned *grid, const unsigned *block, const bool *present,
+                            cudaStream_t main);
+}  // namespace zmc
+
 struct zmc_ctx {
   int device = 0;
   int sms = 0;
   std::string gpu_name;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  zmc::FamilyFork fork;  // concurrent family kernels of one launch
   char *arena_base = nullptr;
   bool own_arena = false;
   zmc::Arena arena;

@@ -104,6 +104,7 @@ struct ServingState {
   std::vector<std::shared_ptr<ServJob>> cancelled_pending;
   uint64_t next_id = 1;
   cudaStream_t stream = nullptr;
+  FamilyFork fork;  // the four family kernels of an iteration run concurrently
   Slot slots[2];
   uint32_t max_chunks = 0;
   uint32_t max_entries = 0;
@@ -168,8 +169,11 @@ zmc_status build_slot_graph(ServingState *S, Slot &sl) {
   cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving capture");
   cudaError_t le = cudaMemsetAsync(sl.d_hdr, 0, sizeof(sl.d_hdr->counter), S->stream);
-  for (int f = 0; f < 4 && le == cudaSuccess; ++f)
-    le = launch_batched(f, sl.d_entries, sl.d_hdr, S->grid[f], ctx->shape.block, S->stream);
+  const bool all[4] = {true, true, true, true};
+  const unsigned block[4] = {ctx->shape.block, ctx->shape.block, ctx->shape.block,
+                             ctx->shape.block};
+  if (le == cudaSuccess)
+    le = launch_families(S->fork, sl.d_entries, sl.d_hdr, S->grid, block, all, S->stream);
   if (le == cudaSuccess) {
     const unsigned mg = static_cast<unsigned>(
         std::min<uint64_t>((S->max_merge + 7) / 8, static_cast<uint64_t>(ctx->sms) * 16));
@@ -534,6 +538,11 @@ zmc_status serving_start(zmc_ctx *ctx) {
   if (const char *f = std::getenv("ZMC_SERVING_FAULT_AT")) S->fault_at = std::strtoull(f, nullptr, 10);
   cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving stream");
+  e = S->fork.init();
+  if (e != cudaSuccess) {
+    S->fork.destroy();
+    return ctx_cuda_fail(ctx, e, "serving side streams");
+  }
   for (int f = 0; f < 4; ++f) S->grid[f] = family_grid(ctx, f, ~0ull >> 8);
   const size_t sb = stage_bytes(S.get());
   for (auto &sl : S->slots) {
@@ -585,6 +594,7 @@ void serving_stop(zmc_ctx *ctx) {
     ctx->arena.release(sl.d_hdr);
   }
   cudaStreamDestroy(S->stream);
+  S->fork.destroy();
   delete S;
   ctx->srv = nullptr;
 }

@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_EAGAIN",
 ZMC_STAGE_SAMPLE, ZMC_STAGE_MERGE, ZMC_STAGE_ALL = 1, 2, 3
 ZMC_USER = 4
 DEFAULT_QUADS_PER_LANE = 64  # the library's default chunk: 128 x 64 = 8192 samples
+SERVING_QUADS_PER_LANE = 32  # ... and for a serving context: 4096 samples
 ZMC_UDF_F32, ZMC_UDF_F64 = 0, 1
 
 RESULT_DTYPE = np.dtype([("estimate", "<f8"), ("stderr", "<f8"), ("n", "<u8"),
@@ -468,7 +469,7 @@ class Context:
     """
 
     def __init__(self, arena_bytes: int = 1 << 30, device: int = 0, stream=None,
-                 serving: bool = False, quads_per_lane: int = DEFAULT_QUADS_PER_LANE,
+                 serving: bool = False, quads_per_lane: int = 0,
                  max_chunks_per_iter: int = 0,
                  use_torch_memory: bool = True, autotune: bool = False,
                  tune_cache_path: str | None = None):

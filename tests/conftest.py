@@ -50,6 +50,17 @@ def zctx():
 
 
 @pytest.fixture(scope="session")
+def sq_ctx(zctx):
+    """A blocking context with a serving context's chunk length, whose results
+    can be compared bit for bit with served ones."""
+    from paper_2104_10073_gb300 import zmc
+
+    ctx = zmc.Context(arena_bytes=2 << 30, quads_per_lane=zmc.SERVING_QUADS_PER_LANE)
+    yield ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="session")
 def curand_philox(tmp_path_factory):
     """Callable (ctr (n,4), key (n,2)) -> words, backed by cuRAND's device Philox."""
     import numpy as np

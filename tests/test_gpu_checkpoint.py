@@ -17,7 +17,7 @@ from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
 
-CHUNK = 128 * zmc.DEFAULT_QUADS_PER_LANE  # samples per chunk at the default
+CHUNK = 128 * zmc.SERVING_QUADS_PER_LANE  # samples per chunk of a serving context
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +55,7 @@ def _checkpoint_mid_run(sctx, t, delay_s):
     return jid, st, ck
 
 
-def test_checkpoint_moments_equal_prefix_moments(sctx, zctx):
+def test_checkpoint_moments_equal_prefix_moments(sctx, sq_ctx):
     """A checkpoint's moments are those of the first n samples of each stream,
     bit for bit the same as zmc_integrate_moments over [0, n)."""
     t = _big_job(seed=1)
@@ -71,16 +71,16 @@ def test_checkpoint_moments_equal_prefix_moments(sctx, zctx):
     st2, _ = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=0)
     assert st2 == zmc.ZMC_ENOTFOUND
     rows = n > 0
-    ref = zmc.zmc_integrate_moments(zctx.handle, t[rows], np.zeros(rows.sum()), n[rows])
+    ref = zmc.zmc_integrate_moments(sq_ctx.handle, t[rows], np.zeros(rows.sum()), n[rows])
     assert np.array_equal(ck["mean"][rows], ref["mean"])
     assert np.array_equal(ck["m2"][rows], ref["m2"])
     assert np.all(ck["mean"][~rows] == 0) and np.all(ck["m2"][~rows] == 0)
 
 
 @pytest.mark.parametrize("delay_s", [0.0, 0.002, 0.01])
-def test_resume_equals_uninterrupted(sctx, zctx, delay_s):
+def test_resume_equals_uninterrupted(sctx, sq_ctx, delay_s):
     t = _big_job(seed=2)
-    want = zmc.zmc_integrate(zctx.handle, t)
+    want = zmc.zmc_integrate(sq_ctx.handle, t)
     jid, st, ck = _checkpoint_mid_run(sctx, t, delay_s)
     if st == zmc.ZMC_EAGAIN:
         st, got = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=120000)
@@ -94,10 +94,10 @@ def test_resume_equals_uninterrupted(sctx, zctx, delay_s):
     _close(got, want, t)
 
 
-def test_chain_of_checkpoints_and_migration(sctx, zctx):
+def test_chain_of_checkpoints_and_migration(sctx, sq_ctx):
     """Checkpoint, resume on another context, checkpoint again, resume back."""
     t = _big_job(n_fn=4, n_samples=1 << 28, seed=3)
-    want = zmc.zmc_integrate(zctx.handle, t)
+    want = zmc.zmc_integrate(sq_ctx.handle, t)
     with zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=1024) as other:
         _, st, ck1 = _checkpoint_mid_run(sctx, t, 0.003)
         assert st == zmc.ZMC_OK
@@ -135,7 +135,7 @@ def test_checkpoint_of_queued_job():
         assert st in (zmc.ZMC_ECLOSED, zmc.ZMC_OK)
 
 
-def test_resume_from_moments_matches_oracle(sctx, zctx):
+def test_resume_from_moments_matches_oracle(sctx, sq_ctx):
     """Resume from zmc_integrate_moments over [0, n) for ragged n (multiples of 4,
     not of the chunk), every family; the result matches the FP64 oracle."""
     rng = np.random.default_rng(11)
@@ -146,7 +146,7 @@ def test_resume_from_moments_matches_oracle(sctx, zctx):
     n0[1::9] = 0          # some start afresh
     from_m = np.zeros(len(t), dtype=zmc.MOMENTS_DTYPE)
     rows = n0 > 0
-    from_m[rows] = zmc.zmc_integrate_moments(zctx.handle, t[rows], np.zeros(rows.sum()),
+    from_m[rows] = zmc.zmc_integrate_moments(sq_ctx.handle, t[rows], np.zeros(rows.sum()),
                                              n0[rows])
     rid = zmc.zmc_submit_resume(sctx.handle, t, from_m)
     st, got = zmc.zmc_poll(sctx.handle, rid, len(t), wait_ms=120000)
@@ -156,13 +156,13 @@ def test_resume_from_moments_matches_oracle(sctx, zctx):
     G.compare(t, got, want)
 
 
-def test_resume_with_nothing_left(sctx, zctx):
+def test_resume_with_nothing_left(sctx, sq_ctx):
     t = W.harmonic_fig1(50000)[:8]
-    full = zmc.zmc_integrate_moments(zctx.handle, t, np.zeros(len(t)), t["n_samples"])
+    full = zmc.zmc_integrate_moments(sq_ctx.handle, t, np.zeros(len(t)), t["n_samples"])
     rid = zmc.zmc_submit_resume(sctx.handle, t, full)
     st, got = zmc.zmc_poll(sctx.handle, rid, len(t), wait_ms=120000)
     assert st == zmc.ZMC_OK
-    want = zmc.zmc_integrate(zctx.handle, t)
+    want = zmc.zmc_integrate(sq_ctx.handle, t)
     _close(got, want, t)
 
 
@@ -200,7 +200,7 @@ def test_checkpoint_after_completion_is_refused(sctx):
     assert st == zmc.ZMC_ENOTFOUND
 
 
-def test_resume_combines_the_given_moments(sctx, zctx):
+def test_resume_combines_the_given_moments(sctx, sq_ctx):
     """The resumed result is Chan's combination of the moments passed in with the
     moments of samples [n, N): planted prior moments (not those of the stream)
     show up in the result exactly as the pairwise update predicts."""
@@ -215,7 +215,7 @@ def test_resume_combines_the_given_moments(sctx, zctx):
     rid = zmc.zmc_submit_resume(sctx.handle, t, prior)
     st, got = zmc.zmc_poll(sctx.handle, rid, len(t), wait_ms=120000)
     assert st == zmc.ZMC_OK
-    rest = zmc.zmc_integrate_moments(zctx.handle, t, na, n_all)
+    rest = zmc.zmc_integrate_moments(sq_ctx.handle, t, na, n_all)
     vol = np.array([np.prod(r["hi"][:r["dim"]] - r["lo"][:r["dim"]]) for r in t])
     nb = n_all - na
     d = rest["mean"] - prior["mean"]

@@ -33,7 +33,7 @@ def _jobs(n_jobs, seed, max_fns=40, hi_exp=5.5):
     return jobs
 
 
-def test_results_same_alone_and_mixed(sctx, zctx):
+def test_results_same_alone_and_mixed(sctx, sq_ctx):
     jobs = _jobs(12, seed=3)
     # alone: one job at a time through the serving loop
     alone = []
@@ -49,9 +49,10 @@ def test_results_same_alone_and_mixed(sctx, zctx):
         assert st == zmc.ZMC_OK
         assert np.array_equal(res["estimate"], a["estimate"])
         assert np.array_equal(res["stderr"], a["stderr"], equal_nan=True)
-    # and the same as the blocking batched call and the oracle
+    # and the same as the blocking batched call with the same chunk length, and
+    # the oracle
     for t, a in zip(jobs[:4], alone[:4]):
-        one = zmc.zmc_integrate(zctx.handle, t)
+        one = zmc.zmc_integrate(sq_ctx.handle, t)
         assert np.array_equal(one["estimate"], a["estimate"])
         want, _ = oracle.integrate(t)
         G.compare(t, a, want)
@@ -100,7 +101,7 @@ def test_cancel(sctx):
 def test_job_larger_than_budget_is_refused():
     with zmc.Context(arena_bytes=64 << 20, serving=True) as c:
         t = W.empty(1)
-        W.harmonic(t[0], 1.0, 1.0, [1.0], [0.0], [1.0], 2**36)  # 2^25 chunks, 256 MiB
+        W.harmonic(t[0], 1.0, 1.0, [1.0], [0.0], [1.0], 2**36)  # 2^24 chunks, 128 MiB of records
         with pytest.raises(zmc.ZmcError) as e:
             zmc.zmc_submit(c.handle, t)
         assert e.value.status == zmc.ZMC_ENOMEM
@@ -109,8 +110,8 @@ def test_job_larger_than_budget_is_refused():
 def test_admission_waits_for_memory():
     """Jobs that do not all fit at once are admitted as earlier ones finish."""
     with zmc.Context(arena_bytes=12 << 20, serving=True, max_chunks_per_iter=4096) as c:
-        chunk = 128 * zmc.DEFAULT_QUADS_PER_LANE
-        n = 2**31 // chunk * chunk  # 2^31 samples: 2 MiB of chunk records per job
+        chunk = 128 * zmc.SERVING_QUADS_PER_LANE
+        n = 2**31 // chunk * chunk  # 2^31 samples: 4 MiB of chunk records per job
         jobs = []
         for j in range(12):
             t = W.empty(1)
@@ -118,7 +119,7 @@ def test_admission_waits_for_memory():
             jobs.append(t)
         ids = [zmc.zmc_submit(c.handle, t) for t in jobs]
         stats = zmc.zmc_serving_stats_get(c.handle)
-        assert stats["queued"] >= 1  # 12 x 2 MiB cannot all be admitted into 12 MiB
+        assert stats["queued"] >= 1  # 12 x 4 MiB cannot all be admitted into 12 MiB
         res = [zmc.zmc_poll(c.handle, i, 1, wait_ms=120000) for i in ids]
         assert all(st == zmc.ZMC_OK for st, _ in res)
         stats = zmc.zmc_serving_stats_get(c.handle)
