@@ -113,3 +113,37 @@ def test_plain_limit_is_direct_monte_carlo():
                seed=int(row["seed"]), stream_base=int(row["stream_id"]), row=row)
     want, _ = oracle.integrate(np.asarray(row).reshape(1))
     assert r["estimate"] == want["estimate"][0] and r["stderr"] == want["stderr"][0]
+
+
+def test_numpy_cells_match_the_c_oracle():
+    """The numpy cell path (mean and M2 by definition) against the C oracle's
+    Welford on the same Eq. 1 integrand: one cell, the plain direct-MC limit."""
+    import oracle
+
+    row = W.harmonic_fig1(20000)[33]
+
+    def harm(x, p):
+        return p[0] * np.cos(x @ p[2:6]) + p[1] * np.sin(x @ p[2:6])
+
+    r = normal(4, row["lo"][:4], row["hi"][:4], divisions=1, depth=0, samples_per_cell=20000,
+               seed=int(row["seed"]), stream_base=int(row["stream_id"]), f=harm,
+               p=np.asarray(row["p"]))
+    want, _ = oracle.integrate(np.asarray(row).reshape(1))
+    assert abs(r["estimate"] - want["estimate"][0]) <= 1e-12 * abs(want["mean_abs"][0])
+    assert abs(r["stderr"] - want["stderr"][0]) <= 1e-10 * want["stderr"][0]
+
+
+def test_children_draw_independent_samples():
+    """After a split the halves' estimates must be independent: for f(x) = x on
+    [0, 1] with the root always split, the spread of the estimate over 300
+    repetitions matches sqrt(sum of the halves' s_c^2) (samples shared between
+    the halves would double the variance)."""
+    est, se = [], []
+    for s in range(300):
+        r = normal(1, [0.0], [1.0], divisions=1, depth=1, samples_per_cell=16, sigma_mult=0.5,
+                   seed=1000 + s, f=lambda x, p: x[:, 0], p=None)
+        assert r["rounds"] == 1 and r["n_leaves"] == 2
+        est.append(r["estimate"])
+        se.append(r["stderr"])
+    ratio = np.var(est, ddof=1) / np.mean(np.square(se))
+    assert 0.75 < ratio < 1.33, ratio
