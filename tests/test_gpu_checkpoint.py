@@ -226,3 +226,58 @@ def test_resume_combines_the_given_moments(sctx, sq_ctx):
     assert np.array_equal(got["n"], n_all.astype(np.uint64))
     assert np.allclose(got["estimate"], est, rtol=1e-13, atol=1e-15 * np.abs(vol).max())
     assert np.allclose(got["stderr"], se, rtol=1e-12)
+
+
+def test_concurrent_submitters_with_checkpoints(sctx, sq_ctx):
+    """Four host threads submit, checkpoint, resume and collect jobs on one
+    serving context at the same time; every final result equals the blocking
+    call's within FP64 rounding of the merge."""
+    import threading
+
+    tables = [_big_job(n_fn=3, n_samples=(1 << 25) + 4096 * k, seed=50 + k) for k in range(8)]
+    want = [zmc.zmc_integrate(sq_ctx.handle, t) for t in tables]
+    errors = []
+
+    def worker(w):
+        try:
+            for k in range(w, len(tables), 4):
+                t = tables[k]
+                jid = zmc.zmc_submit(sctx.handle, t)
+                time.sleep(0.001 * (k % 3))
+                st, ck = zmc.zmc_checkpoint(sctx.handle, jid, len(t), wait_ms=60000)
+                if st == zmc.ZMC_OK:
+                    jid = zmc.zmc_submit_resume(sctx.handle, t, ck)
+                else:
+                    assert st == zmc.ZMC_EAGAIN, st
+                st, got = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=120000)
+                assert st == zmc.ZMC_OK, st
+                _close(got, want[k], t)
+        except BaseException as e:  # reported on the main thread
+            errors.append((w, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(w,)) for w in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(300)
+    assert not any(th.is_alive() for th in threads)
+    assert not errors, errors
+
+
+def test_cancel_during_checkpoint_and_shutdown():
+    """A job cancelled while its checkpoint is pending reports ZMC_ECLOSED, and a
+    context destroyed with jobs and checkpoints outstanding shuts down cleanly."""
+    with zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=256) as c:
+        t = _big_job(n_fn=4, n_samples=1 << 28, seed=77)
+        jid = zmc.zmc_submit(c.handle, t)
+        time.sleep(0.002)
+        st, _ = zmc.zmc_checkpoint(c.handle, jid, len(t), wait_ms=0)
+        assert st in (zmc.ZMC_EAGAIN, zmc.ZMC_OK)
+        if st == zmc.ZMC_EAGAIN:
+            zmc.zmc_cancel(c.handle, jid)
+            st, _ = zmc.zmc_checkpoint(c.handle, jid, len(t), wait_ms=60000)
+            # cancelled while pending (the usual case), or finished / taken first
+            assert st in (zmc.ZMC_ECLOSED, zmc.ZMC_OK, zmc.ZMC_ENOTFOUND, zmc.ZMC_EAGAIN)
+        # leave work behind: the context must still close
+        for k in range(3):
+            zmc.zmc_submit(c.handle, _big_job(n_fn=2, n_samples=1 << 27, seed=80 + k))
