@@ -250,7 +250,10 @@ def run_native(args, world, rank, local):
     from paper_2104_10073_gb300 import build
     from paper_2104_10073_gb300 import zmc
 
-    build.build()
+    # one rank per node compiles (if the sources changed); the others wait
+    if local == 0:
+        build.build()
+    barrier(world)
     torch.cuda.set_device(local)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
