@@ -414,13 +414,13 @@ def run_native(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(zmc, device, rate_hz, seconds, quads_per_lane=0):
+def run_serving(zmc, device, rate_hz, seconds, quads_per_lane=0, chunks_per_iter=0):
     """Poisson job stream through zmc_submit; a collector thread takes finished
     ids from zmc_poll_any and the results from zmc_poll.  Latency = submit call
     to results collected."""
     jobs = W.serving_stream(rate_hz, seconds, max_fns=1000)
     ctx = zmc.Context(arena_bytes=8 << 30, device=device, serving=True,
-                      quads_per_lane=quads_per_lane)
+                      quads_per_lane=quads_per_lane, max_chunks_per_iter=chunks_per_iter)
     submitted = {}
     done = {}
     lock = threading.Lock()
@@ -593,7 +593,8 @@ def run_serving_sweep(args):
     build.build()
     out = []
     for rate in args.serving_rates:
-        r = run_serving(zmc, 0, rate, args.serving_seconds, args.serving_quads)
+        r = run_serving(zmc, 0, rate, args.serving_seconds, args.serving_quads,
+                        args.serving_chunks)
         if r is not None:
             r["demand_gsps"] = rate * 500.5 * 1.444e6 / 1e9  # E[jobs/s x rows x N]
         out.append(r)
@@ -627,6 +628,8 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=10.0)
     ap.add_argument("--serving-quads", type=int, default=0,
                     help="chunk length of the serving context (0: library default)")
+    ap.add_argument("--serving-chunks", type=int, default=0,
+                    help="chunks per serving iteration (0: library default)")
     args = ap.parse_args()
     world, rank, local = (int(os.environ.get("WORLD_SIZE", "1")),
                           int(os.environ.get("RANK", "0")),
