@@ -99,7 +99,12 @@ def test_chain_of_checkpoints_and_migration(sctx, sq_ctx):
     t = _big_job(n_fn=4, n_samples=1 << 28, seed=3)
     want = zmc.zmc_integrate(sq_ctx.handle, t)
     with zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=1024) as other:
-        _, st, ck1 = _checkpoint_mid_run(sctx, t, 0.003)
+        jid, st, ck1 = _checkpoint_mid_run(sctx, t, 0.003)
+        if st == zmc.ZMC_EAGAIN:  # finished before the checkpoint: nothing to chain
+            st, got = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=120000)
+            assert st == zmc.ZMC_OK
+            assert np.array_equal(got["estimate"], want["estimate"])
+            return
         assert st == zmc.ZMC_OK
         rid = zmc.zmc_submit_resume(other.handle, t, ck1)
         time.sleep(0.003)
