@@ -155,12 +155,13 @@ bool quartic_pairs(const double *m, double *a, double *b2) {
 
 bool poly_root_form(const double *e_in, int g, RootForm *out) {
   std::memset(out, 0, sizeof *out);
+  if (g < 0 || g > 4) return false;
   double e[5] = {0, 0, 0, 0, 0};
   for (int k = 0; k <= g; ++k) e[k] = e_in[k];
   while (g > 0 && e[g] == 0.0) --g;
   out->lead = e[g];
   if (g == 0 || e[g] == 0.0) return true;  // a constant (possibly zero)
-  double m[5];
+  double m[5] = {0, 0, 0, 0, 0};
   for (int k = 0; k <= g; ++k) m[k] = e[k] / e[g];
   double roots[4];
   const int nr = real_roots(m, g, roots);
