@@ -169,12 +169,14 @@ def _table(desc) -> np.ndarray:
 
 # ------------------------------------------------------------------ thin wrappers
 def zmc_default_options() -> zmc_options:
+    """The library defaults (zmc_default_options)."""
     o = zmc_options()
     _check(lib().zmc_default_options(ctypes.byref(o)), "zmc_default_options")
     return o
 
 
 def zmc_create(opt: zmc_options | None = None) -> int:
+    """Create a context from a zmc_options (zmc_create); returns the handle."""
     h = ctypes.c_void_p()
     _check(lib().zmc_create(ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)),
            "zmc_create")
@@ -182,14 +184,18 @@ def zmc_create(opt: zmc_options | None = None) -> int:
 
 
 def zmc_destroy(ctx: int) -> None:
+    """Release a context (zmc_destroy)."""
     _check(lib().zmc_destroy(ctx), "zmc_destroy")
 
 
 def zmc_last_error(ctx: int | None = None) -> str:
+    """The reason of the last failure on this thread (zmc_last_error)."""
     return lib().zmc_last_error(ctx).decode()
 
 
 def zmc_integrate(ctx: int, desc) -> np.ndarray:
+    """Blocking batched integration of a descriptor table (zmc_integrate); one
+    RESULT_DTYPE row per descriptor."""
     t = _table(desc)
     out = np.zeros(len(t), dtype=RESULT_DTYPE)
     _check(lib().zmc_integrate(ctx, t.ctypes.data, len(t), out.ctypes.data), "zmc_integrate")
@@ -197,6 +203,8 @@ def zmc_integrate(ctx: int, desc) -> np.ndarray:
 
 
 def zmc_integrate_plain(ctx: int, desc) -> np.ndarray:
+    """The same results computed the plain way, one FP64 launch per integrand
+    (zmc_integrate_plain)."""
     t = _table(desc)
     out = np.zeros(len(t), dtype=RESULT_DTYPE)
     _check(lib().zmc_integrate_plain(ctx, t.ctypes.data, len(t), out.ctypes.data),
@@ -217,14 +225,17 @@ def zmc_integrate_moments(ctx: int, desc, s_begin, s_end) -> np.ndarray:
 
 
 def slot_p(j: int) -> int:
+    """Functional-mode slot of parameter p[j] (ZMC_SLOT_P)."""
     return j
 
 
 def slot_lo(i: int) -> int:
+    """Functional-mode slot of lo[i] (ZMC_SLOT_LO)."""
     return 40 + i
 
 
 def slot_hi(i: int) -> int:
+    """Functional-mode slot of hi[i] (ZMC_SLOT_HI)."""
     return 47 + i
 
 
@@ -243,6 +254,7 @@ def zmc_integrate_functional(ctx: int, base_row, slots, values, independent_stre
 
 
 def zmc_submit(ctx: int, desc) -> int:
+    """Queue a table on a serving context (zmc_submit); returns the job id."""
     t = _table(desc)
     jid = ctypes.c_uint64()
     _check(lib().zmc_submit(ctx, t.ctypes.data, len(t), ctypes.byref(jid)), "zmc_submit")
@@ -269,6 +281,7 @@ def zmc_poll_any(ctx: int, cap: int = 1024, wait_ms: int = -1):
 
 
 def zmc_cancel(ctx: int, job_id: int) -> None:
+    """Cancel a queued or running job (zmc_cancel)."""
     _check(lib().zmc_cancel(ctx, job_id), "zmc_cancel")
 
 
@@ -293,12 +306,14 @@ def zmc_submit_resume(ctx: int, desc, from_moments) -> int:
 
 
 def zmc_serving_stats_get(ctx: int) -> dict:
+    """Counters of the serving loop (zmc_serving_stats_get) as a dict."""
     s = zmc_serving_stats()
     _check(lib().zmc_serving_stats_get(ctx, ctypes.byref(s)), "zmc_serving_stats_get")
     return {name: getattr(s, name) for name, _ in s._fields_}
 
 
 def zmc_plan_create(ctx: int, desc) -> int:
+    """Precompute and upload a table once (zmc_plan_create); returns the plan."""
     t = _table(desc)
     h = ctypes.c_void_p()
     _check(lib().zmc_plan_create(ctx, t.ctypes.data, len(t), ctypes.byref(h)),
@@ -307,26 +322,31 @@ def zmc_plan_create(ctx: int, desc) -> int:
 
 
 def zmc_plan_run(plan: int, stages: int = ZMC_STAGE_ALL) -> None:
+    """Enqueue the plan's stages on the context stream (zmc_plan_run)."""
     _check(lib().zmc_plan_run(plan, stages), "zmc_plan_run")
 
 
 def zmc_plan_run_plain(plan: int) -> None:
+    """Enqueue the plain FP64 form of the plan (zmc_plan_run_plain)."""
     _check(lib().zmc_plan_run_plain(plan), "zmc_plan_run_plain")
 
 
 def zmc_plan_results(plan: int, n: int) -> np.ndarray:
+    """Wait and copy the plan's n results to the host (zmc_plan_results)."""
     out = np.zeros(n, dtype=RESULT_DTYPE)
     _check(lib().zmc_plan_results(plan, out.ctypes.data), "zmc_plan_results")
     return out
 
 
 def zmc_plan_device_results(plan: int) -> int:
+    """Device address of the plan's results (zmc_plan_device_results)."""
     p = ctypes.c_void_p()
     _check(lib().zmc_plan_device_results(plan, ctypes.byref(p)), "zmc_plan_device_results")
     return p.value
 
 
 def zmc_plan_info_get(plan: int) -> dict:
+    """Sizes and launch geometry of a plan (zmc_plan_info_get) as a dict."""
     i = zmc_plan_info()
     _check(lib().zmc_plan_info_get(plan, ctypes.byref(i)), "zmc_plan_info_get")
     out = {}
@@ -337,10 +357,13 @@ def zmc_plan_info_get(plan: int) -> dict:
 
 
 def zmc_plan_destroy(plan: int) -> None:
+    """Release a plan (zmc_plan_destroy)."""
     _check(lib().zmc_plan_destroy(plan), "zmc_plan_destroy")
 
 
 def zmc_philox4x32_10(ctx: int, ctr, key) -> np.ndarray:
+    """Philox4x32-10 of counters (n, 4) under keys (n, 2) by the device routine
+    of the sampling path (zmc_philox4x32_10)."""
     ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
     key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
     out = np.zeros_like(ctr)
@@ -350,6 +373,8 @@ def zmc_philox4x32_10(ctx: int, ctr, key) -> np.ndarray:
 
 
 def zmc_eval_samples(ctx: int, row, s_begin: int, count: int) -> np.ndarray:
+    """FP32 values of samples [s_begin, s_begin + count) of one descriptor, by
+    the sampling path's own generation, map and evaluation (zmc_eval_samples)."""
     t = _table(np.asarray(row).reshape(1))
     out = np.zeros(count, dtype=np.float32)
     _check(lib().zmc_eval_samples(ctx, t.ctypes.data, int(s_begin), int(count),
