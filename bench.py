@@ -315,6 +315,23 @@ def run_native(args, world, rank, local):
         plain_ms = e0.elapsed_time(e1) / plain_steps
     zmc.zmc_plan_destroy(plan)
 
+    # the same FP32 sampling kernels launched one integrand at a time (a plan per
+    # row, replayed as a graph): what batching itself gains, at equal arithmetic
+    per_row_ms = None
+    if not args.skip_plain and rank == 0:
+        rows = [zmc.zmc_plan_create(ctx.handle, tab[i:i + 1]) for i in range(len(tab))]
+        for pr in rows:
+            zmc.zmc_plan_run(pr)
+        ctx.stream.synchronize()
+        e0.record(ctx.stream)
+        for pr in rows:
+            zmc.zmc_plan_run(pr)
+        e1.record(ctx.stream)
+        ctx.stream.synchronize()
+        per_row_ms = e0.elapsed_time(e1)
+        for pr in rows:
+            zmc.zmc_plan_destroy(pr)
+
     # end to end through the public blocking call: host table in, host results out
     e2e_s = None
     if not args.skip_e2e:
@@ -387,6 +404,10 @@ def run_native(args, world, rank, local):
             "value": n_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": plain_ms,
             "dtype": "f64", "form": "one FP64 kernel launch per integrand + merge"},
         "batched_over_plain": None if plain_ms is None else plain_ms / (sum(step_ms) / len(step_ms)),
+        "per_integrand_fp32": None if per_row_ms is None else {
+            "value": n_samples / (per_row_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": per_row_ms,
+            "form": "the batched FP32 kernels, one launch (graph) per integrand",
+            "batched_over_this": per_row_ms / (sum(step_ms) / len(step_ms))},
         "mixed": mixed,
         "functional": functional,
         "checkpoint": checkpoint,
