@@ -374,6 +374,7 @@ def run_native(args, world, rank, local):
         functional = run_functional(zmc, ctx)
         checkpoint = run_checkpoint(zmc, local, ctx)
         udf = run_udf(zmc, ctx)
+        udf["mixed"] = run_udf_mixed(zmc, ctx)
         normal = run_normal(zmc, ctx)
 
     serving = None
@@ -538,6 +539,52 @@ def run_checkpoint(zmc, device, ref_ctx):
             "rows_partial_at_checkpoint": int(np.sum((ck["n"] > 0) & (ck["n"] < tab["n_samples"]))),
             "uninterrupted_ms": 1e3 * t_whole, "checkpoint_resume_ms": 1e3 * t_both,
             "max_abs_diff_in_stderr": float(dev.max())}
+
+
+def run_udf_mixed(zmc, ctx):
+    """The 10^4-integrand mix written as user code: one run-time compiled module
+    of 28 functions (the four forms x dimensions 1..7; the polynomial degree in
+    p[39]), every row selecting its function, one call; FP32 user arithmetic."""
+    forms = {
+        W.HARMONIC: "float ph = 0.0f;\n  for (int i = 0; i < ZMC_UDF_DIM; ++i) ph = fmaf(p[2 + i], x[i], ph);\n"
+                    "  float s, c; sincosf(ph, &s, &c); return p[0] * c + p[1] * s;",
+        W.ABSLIN: "float s = 0.0f;\n  for (int i = 0; i < ZMC_UDF_DIM; ++i) s = fmaf(p[1 + i], x[i], s);\n"
+                  "  return p[0] * fabsf(s);",
+        W.GAUSS: "float r2 = 0.0f;\n  for (int i = 0; i < ZMC_UDF_DIM; ++i) { float t = x[i] - p[2 + i]; r2 = fmaf(t, t, r2); }\n"
+                 "  return p[0] * expf(-r2 / (2.0f * p[1] * p[1]));",
+        W.POLY: "const int g = (int)p[39]; float prod = 1.0f;\n"
+                "  for (int i = 0; i < ZMC_UDF_DIM; ++i) { float q = p[5 * i + 4];\n"
+                "    for (int j = 3; j >= 0; --j) q = (j < g) ? fmaf(q, x[i], p[5 * i + j]) : (j == g ? p[5 * i + j] : q);\n"
+                "    prod *= q; }\n  return prod;",
+    }
+    srcs, dims, index = [], [], {}
+    for fam in (W.HARMONIC, W.ABSLIN, W.GAUSS, W.POLY):
+        for d in range(1, 8):
+            index[(fam, d)] = len(srcs)
+            srcs.append("__device__ float zmc_user_f(const float *x, const float *p) {\n  "
+                        + forms[fam] + "\n}\n")
+            dims.append(d)
+    t0 = time.perf_counter()
+    u = zmc.Udf(srcs, dims, zmc.ZMC_UDF_F32, 0.0)
+    compile_s = time.perf_counter() - t0
+    tab = W.mixed(10**4)
+    fam = tab["family"].copy()
+    tab["p"][:, 39] = tab["deg"]
+    tab["deg"] = [index[(int(f), int(d))] for f, d in zip(fam, tab["dim"])]
+    tab["family"] = W.USER
+    u.integrate(ctx.handle, tab)  # load + warm-up
+    t = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        res = u.integrate(ctx.handle, tab)
+        t.append(time.perf_counter() - t0)
+    assert np.all(res["status"] == 0)
+    u.close()
+    sec = statistics.median(t)
+    n = W.total_samples(tab)
+    return {"workload": "mixed-1e4-integrands as 28 user functions, one call", "samples": n,
+            "value": n / sec / 1e9, "unit": UNIT, "ms": 1e3 * sec, "compile_s": compile_s,
+            "path": "zmc_udf_integrate (host table in, host results out)"}
 
 
 def run_udf(zmc, ctx):

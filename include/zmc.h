@@ -328,12 +328,23 @@ typedef struct zmc_udf zmc_udf;
 zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
                           double amplitude, zmc_udf **out);
 
-/* Integrate n descriptors (host array) with a compiled user integrand: every
- * desc[i].family must be ZMC_USER and desc[i].dim the udf's dimension, at most
- * 7 here (deg is ignored; box, samples, seed, stream and p as for the built-in
- * families; a udf of 8 to 12 dimensions integrates through
- * zmc_normal_integrate_udf).  Results (host array) as zmc_integrate's.
- * Blocking, on the context's stream. */
+/* Several user integrands, each of its own form and dimension, in one module
+ * (the multi-function mode with user code: one launch integrates rows of all of
+ * them).  Function k is sources[k] (each defines its own zmc_user_f; the sources
+ * are compiled in separate namespaces, so helper names may repeat), of dimension
+ * dims[k] and bound amplitudes[k] (amplitudes may be NULL: all 0).  1 <= n_funcs
+ * <= 64; one precision for all.  A row selects function k with desc.deg = k.
+ * Errors name the failing source as zmc_user_source_<k>. */
+zmc_status zmc_udf_create_multi(const char *const *sources, const uint32_t *dims,
+                                uint32_t n_funcs, uint32_t precision, const double *amplitudes,
+                                zmc_udf **out);
+
+/* Integrate n descriptors (host array) with compiled user integrands: every
+ * desc[i].family must be ZMC_USER, desc[i].deg selects the function (0 for a
+ * udf of one function) and desc[i].dim must be that function's dimension, at
+ * most 7 here (box, samples, seed, stream and p as for the built-in families;
+ * functions of 8 to 12 dimensions integrate through zmc_normal_integrate_udf).
+ * Results (host array) as zmc_integrate's.  Blocking, on the context's stream. */
 zmc_status zmc_udf_integrate(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc *desc,
                              size_t n, zmc_result *out);
 
@@ -395,8 +406,9 @@ zmc_status zmc_normal_default_options(zmc_normal_opts *opt);
 zmc_status zmc_normal_integrate(zmc_ctx *ctx, const zmc_desc *base, const zmc_normal_opts *opt,
                                 zmc_normal_result *out);
 
-/* A user-defined integrand of any dimension the udf was compiled for (1..12):
- * lo, hi (udf dim values each) give the box, p the ZMC_NPARAM parameters. */
+/* A user-defined integrand of any dimension the udf was compiled for (1..12;
+ * function 0 of a multi-function udf): lo, hi (its dim values each) give the
+ * box, p the ZMC_NPARAM parameters. */
 zmc_status zmc_normal_integrate_udf(zmc_ctx *ctx, const zmc_udf *udf, const double *lo,
                                     const double *hi, const double *p,
                                     const zmc_normal_opts *opt, zmc_normal_result *out);

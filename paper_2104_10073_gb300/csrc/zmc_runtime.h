@@ -150,7 +150,7 @@ void host_parallel_for(size_t n, size_t grain, const std::function<void(size_t, 
 // hold dim values, p ZMC_NPARAM.
 namespace zmc {
 struct UdfRow {
-  uint32_t dim = 0, stream_id = 0;
+  uint32_t dim = 0, func = 0, stream_id = 0;
   uint64_t n_samples = 0, seed = 0;
   const double *lo = nullptr, *hi = nullptr, *p = nullptr;
 };

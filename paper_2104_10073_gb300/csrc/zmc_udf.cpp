@@ -31,9 +31,9 @@
 using namespace zmc;
 
 struct zmc_udf {
-  uint32_t dim = 0;
+  std::vector<uint32_t> dims;   // per function
+  std::vector<double> scales;   // per function: the kernel sums S f
   uint32_t precision = 0;
-  double scale = 1.0;  // S: the kernel sums S f
   std::vector<char> cubin;
   std::string log;
   mutable std::mutex mu;
@@ -119,9 +119,13 @@ size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 // FnDev of one user integrand (validated).  For ZMC_UDF_F64 the address of its
 // FP64 parameters is filled in by udf_run.
 zmc_status udf_fn(const zmc_udf *u, const UdfRow &d, size_t i, FnDev *fn) {
-  if (d.dim != u->dim)
-    return set_error(ZMC_EINVAL, "row %zu: dim %u, the udf was compiled for %u", i, d.dim,
-                     u->dim);
+  if (d.func >= u->dims.size())
+    return set_error(ZMC_EINVAL, "row %zu: function %u, the udf has %zu", i, d.func,
+                     u->dims.size());
+  if (d.dim != u->dims[d.func])
+    return set_error(ZMC_EINVAL, "row %zu: dim %u, function %u was compiled for %u", i, d.dim,
+                     d.func, u->dims[d.func]);
+  const double scale = u->scales[d.func];
   if (d.n_samples == 0 || d.n_samples > (1ull << 62))
     return set_error(ZMC_EINVAL, "row %zu: n_samples must be in 1..2^62", i);
   std::memset(fn, 0, sizeof *fn);
@@ -149,22 +153,23 @@ zmc_status udf_fn(const zmc_udf *u, const UdfRow &d, size_t i, FnDev *fn) {
     if (f32) put_f32(&fn->w[kUdfF32P + j], d.p[j]);
   }
   if (f32)
-    put_f32(&fn->w[kUdfF32S], u->scale);
+    put_f32(&fn->w[kUdfF32S], scale);
   else
-    put_f64(&fn->w[kUdfF64S], u->scale);
-  fn->variant = variant_code(ZMC_USER, d.dim, 0);
+    put_f64(&fn->w[kUdfF64S], scale);
+  fn->variant = variant_code(ZMC_USER, d.dim, d.func);
   fn->stream_id = d.stream_id;
   fn->key0 = static_cast<uint32_t>(d.seed);
   fn->key1 = static_cast<uint32_t>(d.seed >> 32);
   fn->n_samples = d.n_samples;
   fn->volume = vol;
-  fn->inv_scale = 1.0 / u->scale;  // a power of two: exact
+  fn->inv_scale = 1.0 / scale;  // a power of two: exact
   return ZMC_OK;
 }
 
 UdfRow row_of(const zmc_desc &d) {
   UdfRow r;
   r.dim = d.dim;
+  r.func = d.deg;
   r.stream_id = d.stream_id;
   r.n_samples = d.n_samples;
   r.seed = d.seed;
@@ -335,29 +340,69 @@ zmc_status udf_run(zmc_ctx *ctx, const zmc_udf *udf, const UdfRow *rows, size_t 
   return ZMC_OK;
 }
 
-uint32_t udf_dim(const zmc_udf *udf) { return udf ? udf->dim : 0; }
+uint32_t udf_dim(const zmc_udf *udf) { return udf && !udf->dims.empty() ? udf->dims[0] : 0; }
 
 }  // namespace zmc
 
 extern "C" {
 
-zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
-                          double amplitude, zmc_udf **out) {
-  if (!source || !out) return set_error(ZMC_EINVAL, "null argument");
+zmc_status zmc_udf_create_multi(const char *const *sources, const uint32_t *dims,
+                                uint32_t n_funcs, uint32_t precision, const double *amplitudes,
+                                zmc_udf **out) {
+  if (!sources || !dims || !out) return set_error(ZMC_EINVAL, "null argument");
   *out = nullptr;
-  if (dim < 1 || dim > static_cast<uint32_t>(kUdfMaxDim))
-    return set_error(ZMC_EINVAL, "dim %u not in 1..%d", dim, kUdfMaxDim);
+  if (n_funcs < 1 || n_funcs > 64) return set_error(ZMC_EINVAL, "n_funcs must be in 1..64");
   if (precision != ZMC_UDF_F32 && precision != ZMC_UDF_F64)
     return set_error(ZMC_EINVAL, "precision must be ZMC_UDF_F32 or ZMC_UDF_F64");
-  if (!(amplitude >= 0.0) || !std::isfinite(amplitude))
-    return set_error(ZMC_EINVAL, "amplitude must be finite and >= 0");
+  std::vector<double> scales(n_funcs, 1.0);
+  for (uint32_t k = 0; k < n_funcs; ++k) {
+    if (!sources[k]) return set_error(ZMC_EINVAL, "source %u is null", k);
+    if (dims[k] < 1 || dims[k] > static_cast<uint32_t>(kUdfMaxDim))
+      return set_error(ZMC_EINVAL, "function %u: dim %u not in 1..%d", k, dims[k], kUdfMaxDim);
+    const double a = amplitudes ? amplitudes[k] : 0.0;
+    if (!(a >= 0.0) || !std::isfinite(a))
+      return set_error(ZMC_EINVAL, "function %u: amplitude must be finite and >= 0", k);
+    if (a > 0.0) {
+      int sexp = 48 - static_cast<int>(std::ceil(std::log2(a)));
+      sexp = std::max(-100, std::min(100, sexp));
+      scales[k] = std::ldexp(1.0, sexp);
+    }
+  }
   const Nvrtc &api = nvrtc();
   if (!api.ok) return set_error(ZMC_ENOSYS, "NVRTC unavailable: %s", api.why.c_str());
 
-  std::string prog = "#define ZMC_UDF_DIM " + std::to_string(dim) + "\n" +
-                     "#define ZMC_UDF_PRECISION " + std::to_string(precision) + "\n" +
-                     "#include \"zmc_device.cuh\"\n" + "#line 1 \"zmc_user_source\"\n" +
-                     source + "\n#include \"zmc_udf_kernel.cuh\"\n";
+  // each source in a namespace of its own, then the sampling path, then the
+  // thunks and the (dimension, function) switch
+  std::string prog = "#define ZMC_UDF_PRECISION " + std::to_string(precision) + "\n" +
+                     "#include \"zmc_device.cuh\"\n";
+  for (uint32_t k = 0; k < n_funcs; ++k) {
+    const std::string ks = std::to_string(k);
+    prog += "namespace zmc_user_" + ks + " {\n#define ZMC_UDF_DIM " + std::to_string(dims[k]) +
+            "\n#line 1 \"zmc_user_source_" + ks + "\"\n" + sources[k] +
+            "\n#undef ZMC_UDF_DIM\n}\n";
+  }
+  prog += "#include \"zmc_udf_kernel.cuh\"\nnamespace zmc {\nnamespace {\n";
+  for (uint32_t k = 0; k < n_funcs; ++k) {
+    const std::string ks = std::to_string(k);
+    prog += "template <> struct UserFn<" + ks +
+            "> { __device__ __forceinline__ static UdfReal f(const UdfReal *x, const UdfReal *p) "
+            "{ return ::zmc_user_" + ks + "::zmc_user_f(x, p); } };\n";
+  }
+  std::string item_cases, eval_cases;
+  for (uint32_t k = 0; k < n_funcs; ++k) {
+    const std::string v = "variant_code(ZMC_USER, " + std::to_string(dims[k]) + ", " +
+                          std::to_string(k) + ")";
+    const std::string targs = "<ZMC_USER, " + std::to_string(dims[k]) + ", " + std::to_string(k) + ">";
+    item_cases += "    case " + v + ": run_item" + targs + "(fn, chunk, Q, lane); break;\n";
+    eval_cases += "    case " + v + ": eval_range" + targs + "(fn, s_begin, count, out); break;\n";
+  }
+  prog += "__device__ void udf_dispatch_item(const FnDev *fn, uint64_t chunk, uint32_t Q, "
+          "uint32_t lane) {\n  switch (fn->variant) {\n" + item_cases +
+          "    default: break;\n  }\n}\n"
+          "__device__ void udf_dispatch_eval(const FnDev *fn, uint64_t s_begin, uint32_t count, "
+          "float *out) {\n  switch (fn->variant) {\n" + eval_cases +
+          "    default: break;\n  }\n}\n}  // namespace\n}  // namespace zmc\n";
+
   const char *hdr_text[] = {kJitZmcH,   kJitZmcInternalH, kJitZmcDeviceCuh, kJitZmcUdfKernelCuh,
                             kJitZmcUdfLayoutH, kStdint, kCstdint, kStddef, kCstddef,
                             kCudaRuntime};
@@ -389,16 +434,18 @@ zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
   u->cubin.resize(cb);
   api.cubin(p, u->cubin.data());
   api.destroy(&p);
-  u->dim = dim;
+  u->dims.assign(dims, dims + n_funcs);
+  u->scales = scales;
   u->precision = precision;
   u->log = log;
-  if (amplitude > 0.0) {
-    int sexp = 48 - static_cast<int>(std::ceil(std::log2(amplitude)));
-    sexp = std::max(-100, std::min(100, sexp));
-    u->scale = std::ldexp(1.0, sexp);
-  }
   *out = u;
   return ZMC_OK;
+}
+
+zmc_status zmc_udf_create(const char *source, uint32_t dim, uint32_t precision,
+                          double amplitude, zmc_udf **out) {
+  if (!source || !out) return set_error(ZMC_EINVAL, "null argument");
+  return zmc_udf_create_multi(&source, &dim, 1, precision, &amplitude, out);
 }
 
 const char *zmc_udf_log(const zmc_udf *udf) { return udf ? udf->log.c_str() : ""; }
@@ -414,13 +461,14 @@ zmc_status zmc_udf_integrate(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc *d
                              zmc_result *out) {
   if (!ctx) return set_error(ZMC_EINVAL, "null context");
   if (!udf || !desc || !out || n == 0) return set_error(ZMC_EINVAL, "bad udf_integrate arguments");
-  if (udf->dim > ZMC_MAX_DIM)
-    return set_error(ZMC_EINVAL, "a %u-dimensional udf takes boxes through zmc_normal_integrate_udf",
-                     udf->dim);
   std::vector<UdfRow> rows(n);
   for (size_t i = 0; i < n; ++i) {
     if (desc[i].family != ZMC_USER)
       return set_error(ZMC_EINVAL, "descriptor %zu: family must be ZMC_USER", i);
+    if (desc[i].dim > ZMC_MAX_DIM)
+      return set_error(ZMC_EINVAL,
+                       "descriptor %zu: a descriptor holds at most %d dimensions; integrands "
+                       "of more integrate through zmc_normal_integrate_udf", i, ZMC_MAX_DIM);
     rows[i] = row_of(desc[i]);
   }
   return udf_run(ctx, udf, rows.data(), n, out);
@@ -432,6 +480,7 @@ zmc_status zmc_udf_eval_samples(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc
   if (!udf || !desc || !out) return set_error(ZMC_EINVAL, "null argument");
   if (ctx->poisoned) return set_error(ZMC_ECUDA, "context poisoned by an earlier CUDA error");
   if (desc->family != ZMC_USER) return set_error(ZMC_EINVAL, "family must be ZMC_USER");
+  if (desc->dim > ZMC_MAX_DIM) return set_error(ZMC_EINVAL, "a descriptor holds at most 7 dimensions");
   if (count == 0) return ZMC_OK;
   if (s_begin + count > desc->n_samples)
     return set_error(ZMC_EINVAL, "sample range beyond n_samples");

@@ -1,18 +1,29 @@
-// zmc_udf_kernel.cuh -- the sampling path of a user-defined integrand.  Compiled
-// at run time by NVRTC only, after zmc_device.cuh and the user's source (which
-// defines zmc_user_f); zmc_udf.cpp assembles the program and defines
-// ZMC_UDF_DIM and ZMC_UDF_PRECISION.
+// zmc_udf_kernel.cuh -- the sampling path of user-defined integrands.  Compiled
+// at run time by NVRTC only; zmc_udf.cpp assembles the program: zmc_device.cuh,
+// each user source k in a namespace of its own (zmc_user_<k>, with ZMC_UDF_DIM
+// defined to its dimension), this file with ZMC_UDF_PRECISION defined, then the
+// generated UserFn<k> thunks and the variant switch udf_dispatch_item /
+// udf_dispatch_eval over the (dimension, function) pairs.
 //
 // The generator, the per-chunk sums and the persistent work-list loop are those
 // of the built-in families (zmc_device.cuh); only the evaluation differs:
-// Eval<ZMC_USER, ZMC_UDF_DIM, 0> maps the sample onto the box and calls
-// zmc_user_f; the FnDev payload words it reads are laid out in zmc_udf_layout.h
-// (written by zmc_udf.cpp).  The kernels have C names so that the loader can
-// find them.
+// Eval<ZMC_USER, D, K> maps the sample onto the box and calls function K; the
+// FnDev payload words it reads are laid out in zmc_udf_layout.h (written by
+// zmc_udf.cpp).  The kernels have C names so that the loader can find them.
 #include "zmc_udf_layout.h"
 
 namespace zmc {
 namespace {
+
+#if ZMC_UDF_PRECISION == 0
+typedef float UdfReal;
+#else
+typedef double UdfReal;
+#endif
+
+// UserFn<K>::f(x, p) calls user function K (generated after this file).
+template <int K>
+struct UserFn;
 
 #if ZMC_UDF_PRECISION == 0
 template <int D, int G>
@@ -34,7 +45,7 @@ struct Eval<ZMC_USER, D, G> {
     float x[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) x[i] = fmaf(wd[i], unit_v(r[i]) - 1.0f, lo[i]);  // u exact
-    return S * zmc_user_f(x, p);
+    return S * UserFn<G>::f(x, p);
   }
 };
 #else
@@ -65,21 +76,25 @@ struct Eval<ZMC_USER, D, G> {
       const double u = static_cast<double>(r[i] & 0x7FFFFFu) * 0x1p-23;
       x[i] = fma(wd[i], u, lo[i]);
     }
-    return static_cast<float>(S * zmc_user_f(x, p));
+    return static_cast<float>(S * UserFn<G>::f(x, p));
   }
 };
 #endif
 
+// the (dimension, function) switch, generated after this file
+__device__ void udf_dispatch_item(const FnDev *fn, uint64_t chunk, uint32_t Q, uint32_t lane);
+__device__ void udf_dispatch_eval(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out);
+
 template <>
 __device__ void dispatch_item<ZMC_USER>(const FnDev *fn, uint64_t chunk, uint32_t Q,
                                         uint32_t lane) {
-  run_item<ZMC_USER, ZMC_UDF_DIM, 0>(fn, chunk, Q, lane);
+  udf_dispatch_item(fn, chunk, Q, lane);
 }
 
 template <>
 __device__ void dispatch_eval<ZMC_USER>(const FnDev *fn, uint64_t s_begin, uint32_t count,
                                         float *out) {
-  eval_range<ZMC_USER, ZMC_UDF_DIM, 0>(fn, s_begin, count, out);
+  udf_dispatch_eval(fn, s_begin, count, out);
 }
 
 }  // namespace

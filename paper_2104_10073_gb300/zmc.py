@@ -116,6 +116,8 @@ _SIGS = {
     "zmc_integrate_noalloc": ([_P, ctypes.c_size_t, _P, _P], ctypes.c_int),
     "zmc_udf_create": ([ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                         ctypes.POINTER(_P)], ctypes.c_int),
+    "zmc_udf_create_multi": ([_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P, ctypes.POINTER(_P)],
+                             ctypes.c_int),
     "zmc_udf_integrate": ([_P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "zmc_udf_eval_samples": ([_P, _P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_udf_log": ([_P], ctypes.c_char_p),
@@ -432,13 +434,27 @@ class Udf:
     ``source`` defines ``zmc_user_f(const float *x, const float *p)`` (precision
     ZMC_UDF_F32) or the ``double`` form (ZMC_UDF_F64).  Compiling needs no GPU."""
 
-    def __init__(self, source: str, dim: int, precision: int = ZMC_UDF_F32,
-                 amplitude: float = 0.0):
+    def __init__(self, source, dim, precision: int = ZMC_UDF_F32, amplitude=0.0):
+        """``source`` / ``dim`` / ``amplitude``: one function, or lists of them
+        (zmc_udf_create_multi: a row selects function k with its ``deg`` field)."""
         h = _P()
-        _check(lib().zmc_udf_create(source.encode(), dim, precision, amplitude, ctypes.byref(h)),
-               "zmc_udf_create")
+        if isinstance(source, str):
+            _check(lib().zmc_udf_create(source.encode(), dim, precision, amplitude,
+                                        ctypes.byref(h)), "zmc_udf_create")
+            dims = [dim]
+        else:
+            srcs = [s.encode() for s in source]
+            arr = (ctypes.c_char_p * len(srcs))(*srcs)
+            dims = [int(d) for d in dim]
+            d = np.ascontiguousarray(dims, dtype=np.uint32)
+            amps = np.ascontiguousarray(
+                amplitude if np.ndim(amplitude) else [amplitude] * len(srcs), dtype=np.float64)
+            _check(lib().zmc_udf_create_multi(ctypes.cast(arr, _P), d.ctypes.data, len(srcs),
+                                              precision, amps.ctypes.data, ctypes.byref(h)),
+                   "zmc_udf_create_multi")
         self.handle = h.value
-        self.dim = dim
+        self.dims = dims
+        self.dim = dims[0]
         self.precision = precision
 
     @property

@@ -193,3 +193,68 @@ def test_descriptor_validation(zctx, udfs):
     # the context is still usable
     got = udfs["harm64"].integrate(zctx.handle, t)
     assert np.all(got["status"] == 0)
+
+
+ABSLIN_F32 = r"""
+__device__ float zmc_user_f(const float *x, const float *p) {
+  float s = 0.0f;
+  for (int i = 0; i < ZMC_UDF_DIM; ++i) s = fmaf(p[1 + i], x[i], s);
+  return p[0] * fabsf(s);
+}
+"""
+
+
+def test_multi_function_batch_matches_references(zctx):
+    """Three user functions of different forms and dimensions (Eq. 1 in 4-D,
+    Eq. 2 in 2-D, the rational form in 5-D), their rows interleaved in one
+    table and integrated in one call, against the oracle's families and the
+    numpy reference; each row as when its function is integrated alone."""
+    multi = zmc.Udf([HARMONIC_F32, ABSLIN_F32, RATIONAL_F32], [4, 2, 5], zmc.ZMC_UDF_F32,
+                    [2.0, 8.0, 8.0])
+    rng = np.random.default_rng(90)
+    harm = W.harmonic_fig1(30000)[::9]
+    absl = W.abslin_eq2(20000)[:10]
+    absl = absl[absl["dim"] == 2]
+    rat = W.empty(6)
+    for i in range(6):
+        lo = rng.uniform(-1.0, 0.0, 5)
+        W.set_box(rat[i], lo, lo + rng.uniform(0.5, 2.0, 5))
+        rat[i]["family"], rat[i]["dim"] = W.USER, 5
+        rat[i]["n_samples"], rat[i]["seed"], rat[i]["stream_id"] = 40000 + i, 5, 500 + i
+        rat[i]["p"][0], rat[i]["p"][1:6], rat[i]["p"][8] = 1.5, rng.uniform(0.1, 2.0, 5), 0.3
+    parts = [(_as_user(harm), 0), (_as_user(absl), 1), (rat.copy(), 2)]
+    rows = []
+    for tab, k in parts:
+        tab["deg"] = k
+        rows.extend(list(tab))
+    order = rng.permutation(len(rows))
+    table = W.empty(len(rows))
+    for j, i in enumerate(order):
+        table[j] = rows[i]
+    got = multi.integrate(zctx.handle, table)
+    back = np.empty_like(got)
+    back[order] = got
+    n_h, n_a = len(harm), len(absl)
+    want_h, _ = oracle.integrate(harm)
+    want_a, _ = oracle.integrate(absl)
+    G.compare(harm, back[:n_h], want_h, est_rel=2e-5, se_rel=1e-3)  # FP32 sincosf, |k.x| ~ 95
+    G.compare(absl, back[n_h:n_h + n_a], want_a)
+    G.compare(rat, back[n_h + n_a:], _numpy_results(rat, rational_np))
+    alone = zmc.Udf(RATIONAL_F32, 5, zmc.ZMC_UDF_F32, 8.0)
+    ra = alone.integrate(zctx.handle, _deg0(rat))
+    # the same source compiled alone (another module): the same samples and
+    # formula; FP32 code generation may differ between modules by an ulp
+    assert np.allclose(ra["estimate"], back[n_h + n_a:]["estimate"], rtol=1e-6, atol=0)
+    alone.close()
+    bad = table.copy()
+    bad["deg"][0] = 3  # no function 3
+    with pytest.raises(zmc.ZmcError) as e:
+        multi.integrate(zctx.handle, bad)
+    assert e.value.status == zmc.ZMC_EINVAL
+    multi.close()
+
+
+def _deg0(t):
+    t = t.copy()
+    t["deg"] = 0
+    return t

@@ -78,3 +78,33 @@ def test_arguments_are_validated(dim, prec, amp):
     with pytest.raises(zmc.ZmcError) as e:
         zmc.Udf(F32_SRC, dim, prec, amp)
     assert e.value.status == zmc.ZMC_EINVAL
+
+
+HELPER_A = r"""
+__device__ float helper(float v) { return v * v; }
+__device__ float zmc_user_f(const float *x, const float *p) { return p[0] * helper(x[0]); }
+"""
+HELPER_B = r"""
+__device__ float helper(float v) { return v + 1.0f; }
+__device__ float zmc_user_f(const float *x, const float *p) {
+  float s = 0.0f;
+  for (int i = 0; i < ZMC_UDF_DIM; ++i) s += helper(x[i]);
+  return s;
+}
+"""
+
+
+def test_multi_function_module_compiles_with_repeated_helper_names():
+    u = zmc.Udf([HELPER_A, HELPER_B, F32_SRC], [1, 5, 3], zmc.ZMC_UDF_F32, [1.0, 10.0, 2.0])
+    assert u.dims == [1, 5, 3]
+    u.close()
+
+
+def test_multi_function_error_names_the_source():
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.Udf([HELPER_A, "__device__ float zmc_user_f(const float *x, const float *p) "
+                           "{ return undefined_name; }"], [1, 2])
+    assert e.value.status == zmc.ZMC_EINVAL and "zmc_user_source_1" in str(e.value)
+    with pytest.raises(zmc.ZmcError) as e:
+        zmc.Udf([HELPER_A, HELPER_B], [1, 13])
+    assert e.value.status == zmc.ZMC_EINVAL
