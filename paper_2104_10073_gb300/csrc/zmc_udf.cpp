@@ -417,7 +417,7 @@ zmc_status zmc_udf_create_multi(const char *const *sources, const uint32_t *dims
   // -default-device: the library headers' host prototypes (and unannotated user
   // functions) are taken as device declarations
   const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo",
-                        "-default-device", "-diag-suppress=177"};
+                        "-default-device", "-diag-suppress=177", "--split-compile=0"};
   r = api.compile(p, static_cast<int>(sizeof opts / sizeof opts[0]), opts);
   size_t log_n = 0;
   api.log_size(p, &log_n);
