@@ -21,11 +21,13 @@ namespace zmc {
 constexpr int kMaxDim = 7;
 constexpr int kWarp = 32;
 
-// Variant code: family in bits 4..5, dimension in bits 0..2, polynomial degree in
-// bits 6..8.  The sampling kernel dispatches one specialised body per variant.
+// Variant code: dimension in bits 0..3 (1..12), family in bits 4..6, and in
+// bits 8 and up the polynomial's variant degree (0..7) or the index of a user
+// function in its module (0..63).  The sampling kernel dispatches one
+// specialised body per variant.
 __host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t dim,
                                                     uint32_t deg) {
-  return (family << 4) | dim | (deg << 6);
+  return (deg << 8) | (family << 4) | dim;
 }
 
 // One integrand as the sampling kernel sees it (384 bytes, 16-byte aligned).
