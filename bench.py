@@ -369,6 +369,16 @@ def run_native(args, world, rank, local):
             mixed["batched_over_plain"] = mixed["batched_gsps"] / mixed["plain_gsps"]
         zmc.zmc_plan_destroy(mp)
 
+    # the generator alone: Philox4x32-10 blocks/s, the ceiling of any sampling
+    # kernel (a 4-D sample draws one block); measured after the timed region
+    generator = None
+    if rank == 0:
+        rate = zmc.zmc_philox_rate(ctx.handle, 1 << 35) / 1e9
+        generator = {"philox_blocks_per_s": rate, "unit": "G blocks/s",
+                     "ceiling_4d_samples_per_s": rate,
+                     "kernel": "zmc_philox_rate_kernel (2 x 256-thread blocks per SM)",
+                     "harmonic_over_ceiling": n_samples / (kms / 1e3) / 1e9 / rate}
+
     functional = checkpoint = udf = normal = None
     if rank == 0 and not args.skip_modes:
         functional = run_functional(zmc, ctx)
@@ -428,6 +438,7 @@ def run_native(args, world, rank, local):
                      "peak_basis": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz issue slots",
                      "ops_per_sample": harmonic_ops_per_sample(4),
                      "ncu_pipes": prof["pipes"] if prof else None},
+        "generator": generator,
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": 2 * args.steps,

@@ -290,6 +290,18 @@ zmc_status zmc_plan_destroy(zmc_plan *plan);
 zmc_status zmc_philox4x32_10(zmc_ctx *ctx, const uint32_t *ctr, const uint32_t *key,
                              uint32_t *out, size_t n);
 
+/* Throughput of the generator alone on the context's device: Philox4x32-10
+ * blocks per second (into *blocks_per_second) of a kernel that only draws
+ * blocks, with the sampling kernels' counter layout and launch bound (one wave
+ * of 2 x 256-thread blocks per SM, four independent calls at a time per
+ * thread), timed with CUDA events on the context's stream after one untimed
+ * launch.  n_blocks (1..2^40) is rounded up to a whole number of groups of 4
+ * per thread.  The paper has no counterpart; it measures the ceiling of every
+ * sampling kernel, which draws d / 4 blocks per d-dimensional sample.
+ * ZMC_EINVAL for n_blocks out of range, ZMC_ENOMEM if the arena cannot hold
+ * one word per thread, ZMC_ECUDA on a CUDA error. */
+zmc_status zmc_philox_rate(zmc_ctx *ctx, uint64_t n_blocks, double *blocks_per_second);
+
 /* FP32 values f(x_s) of samples s in [s_begin, s_begin + count) of one
  * integrand, computed by the sampling kernel's own generation, map and
  * evaluation code; out has count floats (host). */

@@ -21,9 +21,9 @@ __device__ __forceinline__ float amp_exp2_neg(float amp, float zh, float zl) {
 // relative error of ~2^-24 Z in a plainly summed Z, i.e. ~Z 4e-8 in f, which
 // the tails of narrow Gaussians (Z of tens) cannot afford.  So t_i is formed as
 // an unevaluated pair th + tl (exact product th = fl(h_hi d), its rounding error,
-// and the small terms), t_i^2 as qh + c with qh = th^2 and c = (qh's error) +
-// 2 th tl, Z as zh + zl with every addition's rounding error kept (TwoSum), and
-// f = A 2^-(zh + zl).  Degree 0 / 1 select how t_i is formed (see FnDev).
+// and the small terms), t_i^2 as a part on a fixed grid (whose sum is exact)
+// plus a small correction, Z as zh + zl, and f = A 2^-(zh + zl).  Degree 0 / 1
+// select how t_i is formed (see FnDev).
 template <int D, int G>
 struct Eval<ZMC_GAUSS, D, G> {
   float hh[D], hl[D], pa[D], pb[D];
@@ -61,18 +61,22 @@ struct Eval<ZMC_GAUSS, D, G> {
         th = s;
         tl = __fadd_rn(__fadd_rn(err, pl), fmaf(hl[i], u, pb[i]));
       }
-      const float qh = __fmul_rn(th, th);
-      const float c = fmaf(__fadd_rn(th, th), tl, fmaf(th, th, -qh));
-      if (i == 0) {
-        zh = qh;
-        zl = c;
+      if (D == 1) {
+        zh = __fmul_rn(th, th);
+        zl = fmaf(__fadd_rn(th, th), tl, fmaf(th, th, -zh));
       } else {
-        // Fast2Sum on (max, min): both terms are >= 0, so the larger goes first
-        const float big = fmaxf(zh, qh), small = fminf(zh, qh);
-        const float s = __fadd_rn(big, small);
-        const float err = __fsub_rn(small, __fsub_rn(s, big));
-        zh = s;
-        zl = __fadd_rn(zl, __fadd_rn(err, c));
+        // t_i^2 = qg + c with qg on the grid of 2^-15: fl(th^2 + 256) has that
+        // spacing while th^2 < 256 and removing the 256 is exact (Sterbenz), so
+        // qg is th^2 rounded once to a multiple of 2^-15, r = th^2 - qg
+        // (|r| <= 2^-16, exact to 2^-40), and c adds 2 th tl.  Multiples of
+        // 2^-15 add exactly in FP32 while the sum stays below 512, so zh needs
+        // no error term; beyond that (or th^2 >= 256) f is below 2^-256 and
+        // flushes to zero anyway.
+        const float qg = __fsub_rn(fmaf(th, th, 256.0f), 256.0f);
+        const float r = fmaf(th, th, -qg);
+        const float c = fmaf(th, tl, fmaf(th, tl, r));
+        zh = (i == 0) ? qg : __fadd_rn(zh, qg);
+        zl = (i == 0) ? c : __fadd_rn(zl, c);
       }
     }
     return amp_exp2_neg(A, zh, zl);

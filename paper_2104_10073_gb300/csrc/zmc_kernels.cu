@@ -14,6 +14,8 @@
 //                        stderr = V sqrt(M2 / (N (N-1))) (Fig. 1 caption: an estimate
 //                        with its spread).
 //   zmc_plain_fp64_kernel  (zmc_plain.cu) the plain form, one launch per integrand.
+//   zmc_philox_rate_kernel  the generator alone (its throughput: the ceiling of
+//                        any sampling kernel, which draws d / 4 blocks per sample).
 //   zmc_philox_kernel, zmc_eval_kernel<FAM>   the generator and the per-sample
 //                        integrand values of the sampling path, for parity tests.
 //
@@ -105,6 +107,28 @@ __global__ void zmc_philox_kernel(const uint32_t *__restrict__ ctr,
   }
 }
 
+// Generator rate: every thread draws per_thread Philox4x32-10 blocks, four
+// independent calls at a time, with the sampling kernels' counter layout (low
+// word advancing; high word, stream word and key the same for the whole warp)
+// and their launch bound, and folds the words into one so that none is dead.
+__global__ void __launch_bounds__(256, 2) zmc_philox_rate_kernel(uint32_t key0, uint32_t key1,
+                                                                 uint32_t sid,
+                                                                 uint32_t per_thread,
+                                                                 uint32_t *__restrict__ out) {
+  const RoundKeys rk = make_round_keys(key0, key1);
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t base = t * per_thread;  // wraps on huge grids: a rate needs no distinct counters
+  uint32_t acc = 0;
+  for (uint32_t q = 0; q < per_thread; q += 4) {
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+      const uint4 o = philox(base + q + j, 0u, sid, 0u, rk);
+      acc ^= o.x ^ o.y ^ o.z ^ o.w;
+    }
+  }
+  out[t] = acc;
+}
+
 const FamilyOps *ops_of(int family) {
   switch (family) {
     case ZMC_HARMONIC:
@@ -146,6 +170,12 @@ cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
   const size_t blocks = (n + 255) / 256;
   zmc_philox_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(
       ctr, key, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_rate(uint32_t per_thread, unsigned grid, uint32_t *out,
+                               cudaStream_t stream) {
+  zmc_philox_rate_kernel<<<grid, 256, 0, stream>>>(0x2104u, 0x10073u, 7u, per_thread, out);
   return cudaGetLastError();
 }
 

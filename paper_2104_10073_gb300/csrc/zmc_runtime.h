@@ -82,6 +82,10 @@ struct FamilyFork {
 cudaError_t launch_families(FamilyFork &ff, const Entry *entries, LaunchHdr *hdr,
                             const unsigned *grid, const unsigned *block, const bool *present,
                             cudaStream_t main);
+// The generator-only kernel (zmc_kernels.cu): grid x 256 threads, per_thread
+// Philox blocks each (a multiple of 4), one folded word per thread into out.
+cudaError_t launch_philox_rate(uint32_t per_thread, unsigned grid, uint32_t *out,
+                               cudaStream_t stream);
 }  // namespace zmc
 
 struct zmc_ctx {

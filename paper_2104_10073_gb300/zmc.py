@@ -111,6 +111,7 @@ _SIGS = {
     "zmc_plan_info_get": ([_P, ctypes.POINTER(zmc_plan_info)], ctypes.c_int),
     "zmc_plan_destroy": ([_P], ctypes.c_int),
     "zmc_philox4x32_10": ([_P, _P, _P, _P, ctypes.c_size_t], ctypes.c_int),
+    "zmc_philox_rate": ([_P, ctypes.c_uint64, _P], ctypes.c_int),
     "zmc_eval_samples": ([_P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_validate": ([_P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "zmc_integrate_noalloc": ([_P, ctypes.c_size_t, _P, _P], ctypes.c_int),
@@ -372,6 +373,13 @@ def zmc_philox4x32_10(ctx: int, ctr, key) -> np.ndarray:
     _check(lib().zmc_philox4x32_10(ctx, ctr.ctypes.data, key.ctypes.data, out.ctypes.data,
                                    ctr.shape[0]), "zmc_philox4x32_10")
     return out
+
+
+def zmc_philox_rate(ctx: int, n_blocks: int = 1 << 35) -> float:
+    """Philox4x32-10 blocks per second of the generator alone (zmc_philox_rate)."""
+    r = ctypes.c_double()
+    _check(lib().zmc_philox_rate(ctx, n_blocks, ctypes.byref(r)), "zmc_philox_rate")
+    return r.value
 
 
 def zmc_eval_samples(ctx: int, row, s_begin: int, count: int) -> np.ndarray:

@@ -382,3 +382,14 @@ def test_mixed_1e4_full_size_sampled_rows(tmp_path):
     pick = np.array(sorted(pick))
     want, _ = oracle.integrate(tab[pick])
     G.compare(tab[pick], got[pick], want)
+
+
+def test_generator_rate_is_measured(zctx):
+    """The generator-only kernel runs and reports a finite positive rate; its
+    arguments are checked."""
+    rate = zmc.zmc_philox_rate(zctx.handle, 1 << 28)
+    assert math.isfinite(rate) and rate > 1e9
+    for bad in (0, (1 << 40) + 1):
+        with pytest.raises(zmc.ZmcError) as e:
+            zmc.zmc_philox_rate(zctx.handle, bad)
+        assert e.value.status == zmc.ZMC_EINVAL
