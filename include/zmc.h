@@ -13,7 +13,7 @@
  *     stderr   = V * sqrt(M2 / (N (N - 1))),            M2 = sum_s (f(x_s) - mean)^2
  * Sample s of an integrand with dimension d, key `seed` and stream `stream_id`
  * uses words w = s*d + i (i < d) of a Philox4x32-10 stream: word w is lane
- * (w mod 4) of Philox4x32-10(counter = (b mod 2^32, b div 2^32, stream_id, 0),
+ * (w mod 4) of Philox4x32-10(counter = (stream_id, b mod 2^32, b div 2^32, 0),
  * key = (seed mod 2^32, seed div 2^32)), b = w div 4, and coordinate i is
  * x_i = lo_i + (hi_i - lo_i) * (word & 0x7FFFFF) * 2^-23.  The results are
  * therefore a pure function of the descriptor table: they do not depend on
@@ -75,7 +75,7 @@ typedef enum zmc_status {
 typedef struct zmc_desc {
     uint32_t family;
     uint32_t dim;
-    uint32_t stream_id; /* Philox counter word 2: selects the integrand's stream */
+    uint32_t stream_id; /* Philox counter word 0: selects the integrand's stream */
     uint32_t deg;
     uint64_t n_samples;
     uint64_t seed;      /* Philox key                                             */

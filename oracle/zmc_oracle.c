@@ -24,7 +24,7 @@
  *
  *   Sampling: integrand f (key = seed, stream = stream_id) consumes the word
  *   stream w = s*d + i (sample s, coordinate i).  Word w is lane (w mod 4) of
- *   Philox4x32-10 applied to counter (b mod 2^32, b div 2^32, stream_id, 0)
+ *   Philox4x32-10 applied to counter (stream_id, b mod 2^32, b div 2^32, 0)
  *   with key (seed mod 2^32, seed div 2^32), b = w div 4.  Philox4x32-10 is
  *   the generator of Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
  *   as easy as 1, 2, 3" (SC'11): ten rounds of the 4x32 S-box with the two
@@ -121,7 +121,7 @@ static uint32_t zo_word(const zo_fn *f, uint64_t w, zo_cache *cache)
 {
     uint64_t b = w >> 2;
     if (!cache->valid || cache->block != b) {
-        uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), f->stream_id, 0u};
+        uint32_t ctr[4] = {f->stream_id, (uint32_t)b, (uint32_t)(b >> 32), 0u};
         uint32_t key[2] = {(uint32_t)f->seed, (uint32_t)(f->seed >> 32)};
         zo_philox4x32_10(ctr, key, cache->words);
         cache->block = b;

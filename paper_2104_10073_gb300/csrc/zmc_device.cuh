@@ -72,25 +72,114 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
   return make_uint4(c0, c1, c2, c3);
 }
 
+// The sample stream's counter is (stream_id, block lo, block hi, 0).  Across the
+// blocks of one chunk only block lo changes, and it sits in counter word 1, which
+// the first round XORs instead of multiplying.  So both products of round 1, the
+// second product of round 2 and the first of round 3 are the same for the whole
+// chunk: StreamPrefix holds what they contribute, formed once per chunk, and a
+// block then costs 16 widening multiplies instead of the 18 that remain when the
+// varying word is multiplied in round 1.
+struct StreamPrefix {
+  uint32_t a;            // round 1: c0' = block lo ^ a
+  uint32_t b;            // round 2: c2' = hi(M0 c0) ^ b
+  uint32_t c, dk, e;     // round 3: c0' = hi(M1 c2) ^ c, c2' = lo(M0 c0 of round 2) ^ dk, c3' = e
+  uint32_t k0[7], k1[7]; // round keys of rounds 4..10
+};
+
+__device__ __forceinline__ StreamPrefix make_stream_prefix(const RoundKeys &rk, uint32_t sid,
+                                                           uint32_t block_hi) {
+  StreamPrefix p;
+  const uint64_t r1a = static_cast<uint64_t>(kPhiloxM0) * sid;
+  const uint64_t r1b = static_cast<uint64_t>(kPhiloxM1) * block_hi;
+  p.a = static_cast<uint32_t>(r1b >> 32) ^ rk.k0[0];
+  const uint32_t r2c2 = static_cast<uint32_t>(r1a >> 32) ^ rk.k1[0];  // 0 in counter word 3
+  const uint64_t r2b = static_cast<uint64_t>(kPhiloxM1) * r2c2;
+  const uint32_t r3c0 = static_cast<uint32_t>(r2b >> 32) ^ static_cast<uint32_t>(r1b) ^ rk.k0[1];
+  p.b = static_cast<uint32_t>(r1a) ^ rk.k1[1];
+  const uint64_t r3a = static_cast<uint64_t>(kPhiloxM0) * r3c0;
+  p.c = static_cast<uint32_t>(r2b) ^ rk.k0[2];
+  p.dk = static_cast<uint32_t>(r3a >> 32) ^ rk.k1[2];
+  p.e = static_cast<uint32_t>(r3a);
+#pragma unroll
+  for (int r = 0; r < 7; ++r) {
+    p.k0[r] = rk.k0[3 + r];
+    p.k1[r] = rk.k1[3 + r];
+  }
+  return p;
+}
+
+// Philox4x32-10 of counter (stream_id, block_lo, block_hi, 0): equal to
+// philox(stream_id, block_lo, block_hi, 0, rk) for the prefix made from rk.
+__device__ __forceinline__ uint4 philox_block(uint32_t block_lo, const StreamPrefix &p) {
+  const uint64_t q0 = static_cast<uint64_t>(kPhiloxM0) * (block_lo ^ p.a);             // round 2
+  const uint64_t q1 = static_cast<uint64_t>(kPhiloxM1) * (static_cast<uint32_t>(q0 >> 32) ^ p.b);  // round 3
+  uint32_t c0 = static_cast<uint32_t>(q1 >> 32) ^ p.c;
+  uint32_t c1 = static_cast<uint32_t>(q1);
+  uint32_t c2 = static_cast<uint32_t>(q0) ^ p.dk;
+  uint32_t c3 = p.e;
+#pragma unroll
+  for (int r = 0; r < 7; ++r) {
+#if ZMC_PHILOX_MULHI
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+#else
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c0;
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c2;
+    const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+    const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+#endif
+    const uint32_t n0 = hi1 ^ c1 ^ p.k0[r];
+    const uint32_t n2 = hi0 ^ c3 ^ p.k1[r];
+    c1 = lo1;
+    c3 = lo0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
 // The 4*D words of one quad (4 consecutive samples starting at a multiple of 4):
 // sample t, coordinate i is word t*D + i, i.e. lane (t*D+i)%4 of Philox block
-// quad*D + (t*D+i)/4.  FAST: the caller guarantees the block index's high word is
-// the same for the whole chunk, so only the low word advances.
-template <int D, bool FAST>
-__device__ __forceinline__ void gen_quad(uint64_t quad, uint32_t base_lo, uint32_t base_hi,
-                                         uint32_t sid, const RoundKeys &rk, uint32_t (&r)[4 * D]) {
+// quad*D + (t*D+i)/4.
+template <int D>
+__device__ __forceinline__ void gen_quad(uint64_t quad, uint32_t sid, const RoundKeys &rk,
+                                         uint32_t (&r)[4 * D]) {
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    uint32_t lo, hi;
-    if (FAST) {
-      lo = base_lo + static_cast<uint32_t>(j);
-      hi = base_hi;
-    } else {
-      const uint64_t b = quad * D + static_cast<uint64_t>(j);
-      lo = static_cast<uint32_t>(b);
-      hi = static_cast<uint32_t>(b >> 32);
-    }
-    const uint4 o = philox(lo, hi, sid, 0u, rk);
+    const uint64_t b = quad * D + static_cast<uint64_t>(j);
+    const uint4 o = philox(sid, static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), 0u, rk);
+    r[4 * j + 0] = o.x;
+    r[4 * j + 1] = o.y;
+    r[4 * j + 2] = o.z;
+    r[4 * j + 3] = o.w;
+  }
+}
+
+// The same words by way of the chunk prefix, made here for every block (the
+// per-sample test path, which thereby checks philox_block for any block hi).
+template <int D>
+__device__ __forceinline__ void gen_quad_prefixed(uint64_t quad, uint32_t sid,
+                                                  const RoundKeys &rk, uint32_t (&r)[4 * D]) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const uint64_t b = quad * D + static_cast<uint64_t>(j);
+    const StreamPrefix sp = make_stream_prefix(rk, sid, static_cast<uint32_t>(b >> 32));
+    const uint4 o = philox_block(static_cast<uint32_t>(b), sp);
+    r[4 * j + 0] = o.x;
+    r[4 * j + 1] = o.y;
+    r[4 * j + 2] = o.z;
+    r[4 * j + 3] = o.w;
+  }
+}
+
+// The same words when the caller guarantees that the block index's high word is
+// the one the prefix was made for: base_lo is the low word of block quad*D.
+template <int D>
+__device__ __forceinline__ void gen_quad_fast(uint32_t base_lo, const StreamPrefix &sp,
+                                              uint32_t (&r)[4 * D]) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const uint4 o = philox_block(base_lo + static_cast<uint32_t>(j), sp);
     r[4 * j + 0] = o.x;
     r[4 * j + 1] = o.y;
     r[4 * j + 2] = o.z;
@@ -175,7 +264,7 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
   const uint64_t quad0 = (fn->s_off + s0) >> 2;  // s_off is a multiple of 4
   const uint64_t block0 = quad0 * D;
   const uint32_t base_lo0 = static_cast<uint32_t>(block0) + lane * D;
-  const uint32_t base_hi = static_cast<uint32_t>(block0 >> 32);
+  const StreamPrefix sp = make_stream_prefix(rk, sid, static_cast<uint32_t>(block0 >> 32));
 
   // running (n, mean, M2) of the lane, merged from blocks of kBlockQuads quads
   float n = 0.0f, mean = 0.0f, m2 = 0.0f;
@@ -188,7 +277,10 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
       const uint32_t ql = lane + 32u * j;
       if (!FAST && 4u * ql >= nc) break;
       uint32_t r[4 * D];
-      gen_quad<D, FAST>(quad0 + ql, base_lo0 + 32u * D * j, base_hi, sid, rk, r);
+      if (FAST)
+        gen_quad_fast<D>(base_lo0 + 32u * D * j, sp, r);
+      else
+        gen_quad<D>(quad0 + ql, sid, rk, r);
       float f[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) f[t] = ev(r + t * D);
@@ -359,7 +451,7 @@ __device__ __forceinline__ void eval_range(const FnDev *fn, uint64_t s_begin, ui
   for (uint64_t q = q_first + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
        q <= q_last; q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
     uint32_t r[4 * D];
-    gen_quad<D, false>(q, 0u, 0u, fn->stream_id, rk, r);
+    gen_quad_prefixed<D>(q, fn->stream_id, rk, r);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const uint64_t s = 4 * q + t;

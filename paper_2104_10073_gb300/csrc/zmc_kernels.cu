@@ -108,21 +108,22 @@ __global__ void zmc_philox_kernel(const uint32_t *__restrict__ ctr,
 }
 
 // Generator rate: every thread draws per_thread Philox4x32-10 blocks, four
-// independent calls at a time, with the sampling kernels' counter layout (low
-// word advancing; high word, stream word and key the same for the whole warp)
-// and their launch bound, and folds the words into one so that none is dead.
+// independent calls at a time, with the sampling kernels' counter layout and
+// chunk prefix (block lo advancing; stream word, block hi and key the same for
+// the whole warp) and their launch bound, and folds the words into one so that
+// none is dead.
 __global__ void __launch_bounds__(256, 2) zmc_philox_rate_kernel(uint32_t key0, uint32_t key1,
                                                                  uint32_t sid,
                                                                  uint32_t per_thread,
                                                                  uint32_t *__restrict__ out) {
-  const RoundKeys rk = make_round_keys(key0, key1);
+  const StreamPrefix sp = make_stream_prefix(make_round_keys(key0, key1), sid, 0u);
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t base = t * per_thread;  // wraps on huge grids: a rate needs no distinct counters
   uint32_t acc = 0;
   for (uint32_t q = 0; q < per_thread; q += 4) {
 #pragma unroll
     for (uint32_t j = 0; j < 4; ++j) {
-      const uint4 o = philox(base + q + j, 0u, sid, 0u, rk);
+      const uint4 o = philox_block(base + q + j, sp);
       acc ^= o.x ^ o.y ^ o.z ^ o.w;
     }
   }

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) zmc_plain_fp64_kernel(const PlainFn fn,
   for (uint64_t q = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; q < nquads;
        q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
     uint32_t r[4 * D];
-    gen_quad<D, false>(q, 0u, 0u, fn.stream_id, rk, r);
+    gen_quad<D>(q, fn.stream_id, rk, r);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       if (4 * q + t < N) {

@@ -8,7 +8,7 @@ oracle disagrees with:
   random and boundary 128-bit counters and 64-bit keys (bit-exact);
 * ``word_layout`` -- the same independent engine at the counter each sample
   coordinate is defined to use (word w = s*d + i, block w div 4, lane w mod 4,
-  counter (block lo, block hi, stream_id, 0), key = seed), including blocks past
+  counter (stream_id, block lo, block hi, 0), key = seed), including blocks past
   2^32;
 * ``bruteforce_small`` -- an exact rational / 40-digit recomputation of the
   estimate and standard error from those independent words for N <= 16;
@@ -60,6 +60,14 @@ def philox_vs_independent(orc, indep, n_random=400):
     assert bad.size == 0, f"Philox mismatch at {bad[:5]}: {got[bad[:1]]} vs {want[bad[:1]]}"
 
 
+def engine_triple(seed, stream_id, block):
+    """(seed, subsequence, offset) of the independent engine for the block the
+    sample stream draws from.  The engine's counter is (offset lo, offset hi,
+    subsequence lo, subsequence hi); the stream's is (stream_id, block lo,
+    block hi, 0), i.e. offset stream_id + 2^32 block lo in subsequence block hi."""
+    return (seed, block >> 32, stream_id | ((block & 0xFFFFFFFF) << 32))
+
+
 def _layout_rows():
     rows = []
     for d, sid, seed in [(1, 0, 0), (2, 7, 1), (3, 12345, 2**40 + 3), (4, 99, 5),
@@ -83,7 +91,7 @@ def word_layout(orc, indep):
             for t in range(count):
                 for i in range(d):
                     w = (s0 + t) * d + i
-                    triples.append((seed, sid, w >> 2))
+                    triples.append(engine_triple(seed, sid, w >> 2))
                     lanes.append(w & 3)
             want = indep(triples)[np.arange(len(lanes)), lanes].reshape(count, d)
             assert np.array_equal(words, want), (d, s0, words, want)
@@ -134,7 +142,7 @@ def bruteforce_small(orc, indep, sizes=(1, 2, 3, 5, 16)):
         for v in wd:
             vol *= v
         nmax = max(sizes)
-        triples = [(int(row["seed"]), int(row["stream_id"]), (s * d + i) >> 2)
+        triples = [engine_triple(int(row["seed"]), int(row["stream_id"]), (s * d + i) >> 2)
                    for s in range(nmax) for i in range(d)]
         words = indep(triples)
         lanes = [(s * d + i) & 3 for s in range(nmax) for i in range(d)]

@@ -108,7 +108,7 @@ def test_poly_relative_accuracy_near_roots(zctx):
 
 
 def test_eval_samples_across_block_index_carry(zctx):
-    """Samples whose Philox block index crosses 2^32 (counter word 1 carries)."""
+    """Samples whose Philox block index crosses 2^32 (counter word 2, block hi, carries)."""
     for d in (1, 3, 7):
         t = W.empty(1)
         W.abslin(t[0], 1.0, [1.0] * d, [0.0] * d, [1.0] * d, 2**36, seed=9, stream_id=4)

@@ -33,11 +33,14 @@ MUTANTS = {
                             "k0 += ZO_PHILOX_W1;\n        k1 += ZO_PHILOX_W0;"),
     "philox_wrong_word": ("uint32_t n2 = hi0 ^ c[3] ^ k1;", "uint32_t n2 = hi0 ^ c[1] ^ k1;"),
     "counter_stream_word": (
-        "uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), f->stream_id, 0u};",
-        "uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), 0u, f->stream_id};"),
+        "uint32_t ctr[4] = {f->stream_id, (uint32_t)b, (uint32_t)(b >> 32), 0u};",
+        "uint32_t ctr[4] = {0u, (uint32_t)b, (uint32_t)(b >> 32), f->stream_id};"),
     "counter_block_hi_dropped": (
-        "uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), f->stream_id, 0u};",
-        "uint32_t ctr[4] = {(uint32_t)b, 0u, f->stream_id, 0u};"),
+        "uint32_t ctr[4] = {f->stream_id, (uint32_t)b, (uint32_t)(b >> 32), 0u};",
+        "uint32_t ctr[4] = {f->stream_id, (uint32_t)b, 0u, 0u};"),
+    "counter_words_swapped": (
+        "uint32_t ctr[4] = {f->stream_id, (uint32_t)b, (uint32_t)(b >> 32), 0u};",
+        "uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), f->stream_id, 0u};"),
     "word_index": ("zo_word(f, s * (uint64_t)f->dim + i, cache)", "zo_word(f, s + i, cache)"),
     "map_width": ("x[i] = f->lo[i] + (f->hi[i] - f->lo[i]) * zo_uniform(r);",
                   "x[i] = f->lo[i] + f->hi[i] * zo_uniform(r);"),
