@@ -74,8 +74,17 @@ def _newest_input() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
+def _flags_stamp() -> str:
+    """The compile flags the library was last built with (tuning knobs included)."""
+    return os.path.join(BUILD, "flags.txt")
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= _newest_input():
+    flags = " ".join(_flags())
+    stamp = _flags_stamp()
+    same_flags = os.path.exists(stamp) and open(stamp).read() == flags
+    if (not force and same_flags and os.path.exists(OUT)
+            and os.path.getmtime(OUT) >= _newest_input()):
         return OUT
     os.makedirs(BUILD, exist_ok=True)
     _write_jit_sources()
@@ -102,6 +111,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, OUT)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return OUT
 
 

@@ -401,6 +401,28 @@ struct MinBlocks {
                                : FAM == ZMC_GAUSS  ? ZMC_MIN_BLOCKS_GAUSS
                                                    : ZMC_MIN_BLOCKS_POLY;
 };
+// Registers per thread each family kernel is capped at (__maxnreg__): by default
+// what ZMC_MIN_BLOCKS_<FAMILY> 256-thread blocks per SM leave; overridable per
+// family, e.g. to fit more 128-thread blocks.
+#ifndef ZMC_MAXNREG_HARMONIC
+#define ZMC_MAXNREG_HARMONIC (65536 / (256 * ZMC_MIN_BLOCKS_HARMONIC))
+#endif
+#ifndef ZMC_MAXNREG_ABSLIN
+#define ZMC_MAXNREG_ABSLIN (65536 / (256 * ZMC_MIN_BLOCKS_ABSLIN))
+#endif
+#ifndef ZMC_MAXNREG_GAUSS
+#define ZMC_MAXNREG_GAUSS (65536 / (256 * ZMC_MIN_BLOCKS_GAUSS))
+#endif
+#ifndef ZMC_MAXNREG_POLY
+#define ZMC_MAXNREG_POLY (65536 / (256 * ZMC_MIN_BLOCKS_POLY))
+#endif
+template <int FAM>
+struct MaxRegs {
+  static constexpr int value = FAM == ZMC_HARMONIC ? ZMC_MAXNREG_HARMONIC
+                               : FAM == ZMC_ABSLIN ? ZMC_MAXNREG_ABSLIN
+                               : FAM == ZMC_GAUSS  ? ZMC_MAXNREG_GAUSS
+                                                   : ZMC_MAXNREG_POLY;
+};
 
 // The LaunchHdr slot a family's kernel drains: its own for the built-in
 // families, slot 0 of a launch of its own for a user-defined integrand.
@@ -432,7 +454,7 @@ __device__ __forceinline__ void batched_loop(const Entry *__restrict__ entries,
 }
 
 template <int FAM>
-__global__ void __launch_bounds__(256, MinBlocks<FAM>::value)
+__global__ void __launch_bounds__(256) __maxnreg__(MaxRegs<FAM>::value)
     zmc_batched_kernel(const Entry *__restrict__ entries, LaunchHdr *__restrict__ hdr) {
   batched_loop<FAM>(entries, hdr);
 }
