@@ -44,10 +44,10 @@ WORKLOAD = "fig1-harmonics-100x1e6-x10-repeats"
 # three-way XORs) per 4 words -> 10 d; per coordinate: 23-bit mask, the high-word
 # phase multiply-add, the low-word FMA and the add of its bits -> 4 d; the phase
 # carry, |x|, 1/4 - |x|, the integer -> float conversion and its scaling -> 5;
-# t^2, the degree-5 odd polynomial (5) and the amplitude (2) -> 8; shifted
-# sums -> 3.
+# t^2, the degree-4 polynomial in t^2 with the amplitude in its coefficients (4)
+# and the product with t -> 6; shifted sums -> 3.
 def harmonic_ops_per_sample(d: int) -> int:
-    return 10 * d + 4 * d + 5 + 8 + 3
+    return 10 * d + 4 * d + 5 + 6 + 3
 
 
 # Sources of the dominant kernel (zmc_batched_kernel<HARMONIC>).

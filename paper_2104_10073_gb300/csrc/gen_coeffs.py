@@ -1,9 +1,11 @@
 """Fit the FP32 polynomials the kernels evaluate instead of library calls.
 
-* sin(2 pi t) / t on |t| <= 1/4 turn, degree 5 in z = t^2 (relative error):
+* sin(2 pi t) / t on |t| <= 1/4 turn, degree 4 in z = t^2 (relative error):
   the harmonic family writes cos(2 pi x) = sin(2 pi (1/4 - |x|)) for its
-  fixed-point phase x in [-1/2, 1/2) turn and evaluates R t P(t^2), which keeps
-  the relative accuracy near the zeros.
+  fixed-point phase x in [-1/2, 1/2) turn and evaluates t (R P)(t^2), which
+  keeps the relative accuracy near the zeros.  Degree 4 approximates to 5e-9,
+  far below the rounding of its coefficients to binary32 (4e-8; degree 5:
+  2e-11 and 5e-8), so a fifth term would only cost an FMA.
 
 Every fit is a Remez exchange carried out in 50-digit arithmetic, then rounded to
 binary32.  The script prints the maximum error of the rounded polynomials
@@ -66,7 +68,7 @@ def main():
         t = mpmath.sqrt(z)
         return 2 * mpmath.pi if t == 0 else mpmath.sin(2 * mpmath.pi * t) / t
 
-    sq = remez(sinc2, lambda z: 1 / sinc2(z), 6, mpmath.mpf(0), zq)
+    sq = remez(sinc2, lambda z: 1 / sinc2(z), 5, mpmath.mpf(0), zq)
     sq32 = [np.float32(float(v)) for v in sq]
     t = np.linspace(1e-6, 0.25, 200001)
     z = t * t
@@ -77,7 +79,7 @@ def main():
     lines = [
         "// Generated by gen_coeffs.py: Remez fits rounded to binary32.  Max error of the",
         "// rounded polynomials in exact arithmetic:",
-        f"//   sin(2 pi t), |t| <= 1/4 (t times degree 5 in t^2): {es:.2e} relative",
+        f"//   sin(2 pi t), |t| <= 1/4 (t times degree 4 in t^2): {es:.2e} relative",
         "#pragma once",
     ]
     for j, v in enumerate(sq32):

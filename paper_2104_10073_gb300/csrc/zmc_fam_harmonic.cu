@@ -16,14 +16,15 @@ namespace {
 // multiply-add each); the low-word contribution (< 2^23 units) is formed by one
 // FP32 FMA from v' = 2^23 + m_i, whose rounding and the dropped carries cost at
 // most D units of 2^-32 turn.  So |k.x| of any size costs no accuracy.  Then
-// cos(2 pi x) = sin(2 pi (1/4 - |x|)), evaluated as t P(t^2) with a degree-5
-// polynomial P.
+// R cos(2 pi x) = R sin(2 pi (1/4 - |x|)), evaluated as t Pr(t^2) with Pr = R P,
+// P the degree-4 polynomial of zmc_coeffs.h: the amplitude goes into the
+// coefficients once per chunk instead of into every sample.
 template <int D, int G>
 struct Eval<ZMC_HARMONIC, D, G> {
   uint32_t thi[D];
   float tlo[D], kc[D];
   uint32_t p0;
-  float R;
+  float rc[5];  // R times the coefficients of P
   __device__ __forceinline__ void load(const FnDev *fn) {
 #pragma unroll
     for (int i = 0; i < D; ++i) {
@@ -32,7 +33,12 @@ struct Eval<ZMC_HARMONIC, D, G> {
       kc[i] = __uint_as_float(fn->w[14 + i]);
     }
     p0 = fn->w[21];
-    R = __uint_as_float(fn->w[22]);
+    const float R = __uint_as_float(fn->w[22]);
+    rc[0] = R * ZMC_SINQ_C0;
+    rc[1] = R * ZMC_SINQ_C1;
+    rc[2] = R * ZMC_SINQ_C2;
+    rc[3] = R * ZMC_SINQ_C3;
+    rc[4] = R * ZMC_SINQ_C4;
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
     uint32_t acc = p0, lows = 0;
@@ -53,12 +59,11 @@ struct Eval<ZMC_HARMONIC, D, G> {
     const int32_t y = static_cast<int32_t>(0x40000000u - ax);
     const float t = __int2float_rn(y) * 0x1p-32f;
     const float z = t * t;
-    float p = fmaf(ZMC_SINQ_C5, z, ZMC_SINQ_C4);
-    p = fmaf(p, z, ZMC_SINQ_C3);
-    p = fmaf(p, z, ZMC_SINQ_C2);
-    p = fmaf(p, z, ZMC_SINQ_C1);
-    p = fmaf(p, z, ZMC_SINQ_C0);
-    return (R * t) * p;
+    float p = fmaf(rc[4], z, rc[3]);
+    p = fmaf(p, z, rc[2]);
+    p = fmaf(p, z, rc[1]);
+    p = fmaf(p, z, rc[0]);
+    return t * p;
   }
 };
 
