@@ -401,9 +401,10 @@ struct MinBlocks {
                                : FAM == ZMC_GAUSS  ? ZMC_MIN_BLOCKS_GAUSS
                                                    : ZMC_MIN_BLOCKS_POLY;
 };
-// Registers per thread each family kernel is capped at (__maxnreg__): by default
-// what ZMC_MIN_BLOCKS_<FAMILY> 256-thread blocks per SM leave; overridable per
-// family, e.g. to fit more 128-thread blocks.
+// Registers per thread each family kernel is capped at (__maxnreg__, which
+// cannot be combined with __launch_bounds__; the kernels are launched with 128 or
+// 256 threads): by default what ZMC_MIN_BLOCKS_<FAMILY> 256-thread blocks per SM
+// leave; overridable per family, e.g. to fit more 128-thread blocks.
 #ifndef ZMC_MAXNREG_HARMONIC
 #define ZMC_MAXNREG_HARMONIC (65536 / (256 * ZMC_MIN_BLOCKS_HARMONIC))
 #endif
@@ -454,7 +455,7 @@ __device__ __forceinline__ void batched_loop(const Entry *__restrict__ entries,
 }
 
 template <int FAM>
-__global__ void __launch_bounds__(256) __maxnreg__(MaxRegs<FAM>::value)
+__global__ void __maxnreg__(MaxRegs<FAM>::value)
     zmc_batched_kernel(const Entry *__restrict__ entries, LaunchHdr *__restrict__ hdr) {
   batched_loop<FAM>(entries, hdr);
 }
