@@ -511,6 +511,12 @@ int max_blocks_family(int block) {
 }
 
 template <int FAM>
+int regs_family() {
+  cudaFuncAttributes a{};
+  return cudaFuncGetAttributes(&a, zmc_batched_kernel<FAM>) == cudaSuccess ? a.numRegs : 0;
+}
+
+template <int FAM>
 cudaError_t launch_eval_family(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out,
                                cudaStream_t stream) {
   if (count == 0) return cudaSuccess;
@@ -524,7 +530,7 @@ cudaError_t launch_eval_family(const FnDev *fn, uint64_t s_begin, uint32_t count
 template <int FAM>
 constexpr FamilyOps family_ops() {
   return FamilyOps{&launch_batched_family<FAM>, &max_blocks_family<FAM>,
-                   &launch_eval_family<FAM>};
+                   &launch_eval_family<FAM>, &regs_family<FAM>};
 }
 
 #endif  // __CUDACC_RTC__

@@ -134,6 +134,7 @@ struct FamilyOps {
   int (*max_blocks_per_sm)(int block);  // resident blocks of `block` threads per SM
   cudaError_t (*launch_eval)(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out,
                              cudaStream_t stream);
+  int (*regs_per_thread)();  // registers of the family kernel as built (0 if unknown)
 };
 extern const FamilyOps kFamilyHarmonic, kFamilyAbslin, kFamilyGauss, kFamilyPoly;
 
@@ -151,6 +152,7 @@ cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
 cudaError_t launch_eval(int family, const FnDev *fn, uint64_t s_begin, uint32_t count,
                         float *out, cudaStream_t stream);
 int batched_max_blocks_per_sm(int family, int block);
+int batched_regs_per_thread(int family);
 unsigned plain_grid(const PlainFn &fn, int sms);
 #endif  // __CUDACC_RTC__
 

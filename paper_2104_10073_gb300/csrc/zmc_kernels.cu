@@ -165,6 +165,11 @@ int batched_max_blocks_per_sm(int family, int block) {
   return ops ? ops->max_blocks_per_sm(block) : 0;
 }
 
+int batched_regs_per_thread(int family) {
+  const FamilyOps *ops = ops_of(family);
+  return ops ? ops->regs_per_thread() : 0;
+}
+
 cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, size_t n,
                           cudaStream_t stream) {
   if (n == 0) return cudaSuccess;

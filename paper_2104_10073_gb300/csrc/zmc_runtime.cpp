@@ -896,7 +896,10 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   ctx->autotune = opt.autotune != 0;
   if (opt.tune_cache_path) ctx->tune_cache_path = opt.tune_cache_path;
   tune_cache_load(ctx.get());
-  for (int f = 0; f < 4; ++f) ctx->max_blocks_per_sm[f] = batched_max_blocks_per_sm(f, 256);
+  for (int f = 0; f < 4; ++f) {
+    ctx->max_blocks_per_sm[f] = batched_max_blocks_per_sm(f, 256);
+    ctx->kernel_regs[f] = batched_regs_per_thread(f);
+  }
   e = ctx->fork.init();
   if (e != cudaSuccess) {
     ctx->fork.destroy();

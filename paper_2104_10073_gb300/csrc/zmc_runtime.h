@@ -104,6 +104,7 @@ struct zmc_ctx {
   std::string tune_cache_path;
   zmc::LaunchShape shape;
   int max_blocks_per_sm[4] = {0, 0, 0, 0};
+  int kernel_regs[4] = {0, 0, 0, 0};  // registers per thread of each family kernel
   std::map<std::string, zmc::TuneChoice> tune_cache;  // autotuner results by key
   std::atomic<bool> poisoned{false};
   std::recursive_mutex api_mu;  // serialises API calls that use the stream
