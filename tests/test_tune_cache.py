@@ -1,5 +1,6 @@
 """The autotuner's JSON cache, on the host (CPU only): every entry survives a
-load / store / reload round trip, malformed entries are skipped."""
+load / store / reload round trip, malformed entries are skipped, and the key
+names the family kernel's registers per thread (its build)."""
 import os
 import subprocess
 
@@ -23,6 +24,8 @@ def test_cache_round_trip(tmp_path):
                    '}}\n')
     out = subprocess.run([exe, str(src), str(tmp_path / "out.json")], capture_output=True,
                          text=True, check=True).stdout.splitlines()
+    assert out[-1] == "key: GPU X|10|2|16|5|r115"
+    out = out[:-1]
     assert sorted(out) == sorted(["NVIDIA GB300|152|0|16|4 256 2",
                                   "NVIDIA GB300|152|1|16|6 128 4",
                                   "NVIDIA GB300|152|3|16|7 128 4",
