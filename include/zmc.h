@@ -28,6 +28,11 @@
  *     unusable (every later call on it returns ZMC_ECUDA); destroy it.
  *   - A context serialises its calls internally; different contexts are
  *     independent.
+ *   - A table of descriptors holds n >= 1 rows: an empty table (n = 0) is
+ *     rejected with ZMC_EINVAL by every call that integrates, plans or submits
+ *     it, since there is nothing to integrate.  zmc_validate accepts it (no row
+ *     is invalid); the test calls zmc_philox4x32_10 (n = 0) and
+ *     zmc_eval_samples (count = 0) return ZMC_OK without computing anything.
  */
 #ifndef ZMC_H
 #define ZMC_H

@@ -88,6 +88,11 @@ def test_validation_family_specific(lib):
     assert zmc.zmc_validate(t)[0] == zmc.ZMC_OK
 
 
+def test_validation_of_an_empty_table(lib):
+    st, bad, _ = zmc.zmc_validate(W.empty(0))
+    assert st == zmc.ZMC_OK and bad is None
+
+
 def test_validation_accepts_paper_workloads(lib):
     for t in (W.harmonic_fig1(), W.abslin_eq2(), W.mixed(300)):
         assert zmc.zmc_validate(t)[0] == zmc.ZMC_OK

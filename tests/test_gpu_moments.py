@@ -70,6 +70,33 @@ def test_unaligned_pieces_match_oracle_moments(zctx):
             assert abs(m["m2"][k] - m2) <= 1e-4 * m2 + 2e-6 * scale * scale * math.sqrt(n)
 
 
+def test_ranges_across_the_block_index_carry(zctx):
+    """Sample ranges on both sides of Philox block 2^32 (counter word 2, block
+    hi, becomes 1): chunks wholly past it run the per-chunk prefix with block
+    hi = 1, the chunk that straddles it the general counter; against the
+    oracle's moments of the same ranges, for every family."""
+    rng = np.random.default_rng(36)
+    rows, b, e = [], [], []
+    for fam in (W.HARMONIC, W.ABSLIN, W.GAUSS, W.POLY):
+        for d in (1, 3, 4, 7):
+            t = W.random_table(1, rng, n_lo=2**36, n_hi=2**36, families=[fam], dims=[d],
+                               seed=fam * 10 + d)
+            s_carry = -(-(2**32) // d) * 4  # first sample whose blocks start past 2^32
+            a = (s_carry - 3 * CHUNK - 4 * d) // 4 * 4
+            rows.append(t[0]), b.append(a), e.append(a + 7 * CHUNK + 13)
+    tab = W.empty(len(rows))
+    for i, r in enumerate(rows):
+        tab[i] = r
+        tab[i]["stream_id"] = i
+    m = zmc.zmc_integrate_moments(zctx.handle, tab, b, e)
+    for k in range(len(tab)):
+        n, mean, m2, sum_abs = oracle.moments(tab[k], b[k], e[k])
+        assert m["n"][k] == n
+        scale = sum_abs / n
+        assert abs(m["mean"][k] - mean) <= 1e-6 * scale + 2.0**-100 * G.sample_scale(tab[k])
+        assert abs(m["m2"][k] - m2) <= 1e-4 * m2 + 2e-6 * scale * scale * math.sqrt(n)
+
+
 def test_progressive_refinement_extends_the_stream(zctx):
     """[0, N) and [N, 2N) merged equal a run with 2N samples."""
     base = W.random_table(12, np.random.default_rng(34), n_lo=CHUNK, n_hi=20 * CHUNK)

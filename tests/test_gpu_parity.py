@@ -324,6 +324,24 @@ def test_special_cases(zctx):
     G.compare(t, got, want)
 
 
+def test_empty_inputs(zctx):
+    """An empty table is rejected by every call that integrates or plans it;
+    zero-length test calls compute nothing; the context stays usable."""
+    empty = W.empty(0)
+    for call in (zmc.zmc_integrate, zmc.zmc_integrate_plain, zmc.zmc_plan_create):
+        with pytest.raises(zmc.ZmcError) as e:
+            call(zctx.handle, empty)
+        assert e.value.status == zmc.ZMC_EINVAL
+    words = zmc.zmc_philox4x32_10(zctx.handle, np.zeros((0, 4), np.uint32),
+                                  np.zeros((0, 2), np.uint32))
+    assert words.shape == (0, 4)
+    t = W.harmonic_fig1(1000)[:1].copy()
+    assert zmc.zmc_eval_samples(zctx.handle, t[0], 0, 0).shape == (0,)
+    got = zmc.zmc_integrate(zctx.handle, t)
+    want, _ = oracle.integrate(t)
+    G.compare(t, got, want)
+
+
 def test_invalid_descriptor_is_rejected(zctx):
     t = W.harmonic_fig1(10)[:2].copy()
     t[1]["dim"] = 0
