@@ -41,13 +41,14 @@ WORKLOAD = "fig1-harmonics-100x1e6-x10-repeats"
 # Algorithmic 32-bit operations per sample of a d-dimensional harmonic (the
 # dominant kernel of the default workload), counted from the minimal steps of
 # the kernel's method: Philox4x32-10 = 10 rounds x (2 widening multiplies + 2
-# three-way XORs) per 4 words -> 10 d; per coordinate: 23-bit mask, the high-word
-# phase multiply-add, the low-word FMA and the add of its bits -> 4 d; the phase
-# carry, |x|, 1/4 - |x|, the integer -> float conversion and its scaling -> 5;
-# t^2, the degree-4 polynomial in t^2 with the amplitude in its coefficients (4)
-# and the product with t -> 6; shifted sums -> 3.
-def harmonic_ops_per_sample(d: int) -> int:
-    return 10 * d + 4 * d + 5 + 6 + 3
+# three-way XORs) per block of five 23-bit coordinates -> 8 d, and the four shifts
+# that split a block into its fields -> 0.8 d; per coordinate: 23-bit mask, the
+# high-word phase multiply-add, the low-word FMA and the add of its bits -> 4 d;
+# the phase carry, |x|, 1/4 - |x|, the integer -> float conversion and its scaling
+# -> 5; t^2, the degree-4 polynomial in t^2 with the amplitude in its
+# coefficients (4) and the product with t -> 6; shifted sums -> 3.
+def harmonic_ops_per_sample(d: int) -> float:
+    return 8 * d + 0.8 * d + 4 * d + 5 + 6 + 3
 
 
 # Sources of the dominant kernel (zmc_batched_kernel<HARMONIC>).
@@ -273,7 +274,7 @@ def run_native(args, world, rank, local):
 
     tune_path = os.path.join(tempfile.gettempdir(), f"zmc_tune_{os.getuid()}_{local}.json")
     ctx = zmc.Context(arena_bytes=2 << 30, device=local, autotune=not args.no_autotune,
-                      tune_cache_path=tune_path, quads_per_lane=args.quads_per_lane)
+                      tune_cache_path=tune_path, quints_per_lane=args.quints_per_lane)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     tab = fig1_table(rank)
     n_samples = W.total_samples(tab)
@@ -370,14 +371,14 @@ def run_native(args, world, rank, local):
         zmc.zmc_plan_destroy(mp)
 
     # the generator alone: Philox4x32-10 blocks/s, the ceiling of any sampling
-    # kernel (a 4-D sample draws one block); measured after the timed region
+    # kernel (a 4-D sample draws 4/5 of a block); measured after the timed region
     generator = None
     if rank == 0:
         rate = zmc.zmc_philox_rate(ctx.handle, 1 << 35) / 1e9
         generator = {"philox_blocks_per_s": rate, "unit": "G blocks/s",
-                     "ceiling_4d_samples_per_s": rate,
+                     "ceiling_4d_samples_per_s": rate * 5 / 4,
                      "kernel": "zmc_philox_rate_kernel (2 x 256-thread blocks per SM)",
-                     "harmonic_over_ceiling": n_samples / (kms / 1e3) / 1e9 / rate}
+                     "harmonic_over_ceiling": n_samples / (kms / 1e3) / 1e9 / (rate * 5 / 4)}
 
     functional = checkpoint = udf = normal = None
     if rank == 0 and not args.skip_modes:
@@ -407,7 +408,7 @@ def run_native(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "integrands": len(tab), "samples_per_step": n_samples,
-                   "quads_per_lane": info["quads_per_lane"], "chunks": info["n_chunks"],
+                   "quints_per_lane": info["quints_per_lane"], "chunks": info["n_chunks"],
                    "grid": info["family_grid"][0], "block": info["family_block"][0],
                    "autotune": ["default", "measured", "cached"][info["tune_source"][0]],
                    "l2": "flushed between steps (256 MiB write, outside the timed events)"},
@@ -447,13 +448,13 @@ def run_native(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(zmc, device, rate_hz, seconds, quads_per_lane=0, chunks_per_iter=0):
+def run_serving(zmc, device, rate_hz, seconds, quints_per_lane=0, chunks_per_iter=0):
     """Poisson job stream through zmc_submit; a collector thread takes finished
     ids from zmc_poll_any and the results from zmc_poll.  Latency = submit call
     to results collected."""
     jobs = W.serving_stream(rate_hz, seconds, max_fns=1000)
     ctx = zmc.Context(arena_bytes=8 << 30, device=device, serving=True,
-                      quads_per_lane=quads_per_lane, max_chunks_per_iter=chunks_per_iter)
+                      quints_per_lane=quints_per_lane, max_chunks_per_iter=chunks_per_iter)
     submitted = {}
     done = {}
     lock = threading.Lock()
@@ -672,7 +673,7 @@ def run_serving_sweep(args):
     build.build()
     out = []
     for rate in args.serving_rates:
-        r = run_serving(zmc, 0, rate, args.serving_seconds, args.serving_quads,
+        r = run_serving(zmc, 0, rate, args.serving_seconds, args.serving_quints,
                         args.serving_chunks)
         if r is not None:
             r["demand_gsps"] = rate * 500.5 * 1.444e6 / 1e9  # E[jobs/s x rows x N]
@@ -697,15 +698,15 @@ def main():
                          "stratified (normal-mode) legs")
     ap.add_argument("--cpu-repeats", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--quads-per-lane", type=int, default=64,
-                    help="chunk length = 128 x this many samples")
+    ap.add_argument("--quints-per-lane", type=int, default=64,
+                    help="chunk length = 160 x this many samples")
     ap.add_argument("--serving-sweep", action="store_true")
     ap.add_argument("--serving-rates", type=float, nargs="+",
                     default=[10.0, 30.0, 100.0, 300.0, 1000.0])
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=100.0)
     ap.add_argument("--serving-seconds", type=float, default=10.0)
-    ap.add_argument("--serving-quads", type=int, default=0,
+    ap.add_argument("--serving-quints", type=int, default=0,
                     help="chunk length of the serving context (0: library default)")
     ap.add_argument("--serving-chunks", type=int, default=0,
                     help="chunks per serving iteration (0: library default)")

@@ -12,10 +12,11 @@
  *     estimate = V * mean,   V = prod_i (hi_i - lo_i),  mean = (1/N) sum_s f(x_s)
  *     stderr   = V * sqrt(M2 / (N (N - 1))),            M2 = sum_s (f(x_s) - mean)^2
  * Sample s of an integrand with dimension d, key `seed` and stream `stream_id`
- * uses words w = s*d + i (i < d) of a Philox4x32-10 stream: word w is lane
- * (w mod 4) of Philox4x32-10(counter = (stream_id, b mod 2^32, b div 2^32, 0),
- * key = (seed mod 2^32, seed div 2^32)), b = w div 4, and coordinate i is
- * x_i = lo_i + (hi_i - lo_i) * (word & 0x7FFFFF) * 2^-23.  The results are
+ * uses 23-bit fields c = s*d + i (i < d) of a Philox4x32-10 stream: field c is
+ * bits 23k .. 23k+22 (k = c mod 5) of the 128-bit output, word 0 least
+ * significant, of Philox4x32-10(counter = (stream_id, b mod 2^32, b div 2^32, 0),
+ * key = (seed mod 2^32, seed div 2^32)), b = c div 5, and coordinate i is
+ * x_i = lo_i + (hi_i - lo_i) * field * 2^-23.  The results are
  * therefore a pure function of the descriptor table: they do not depend on
  * launch configuration, on which other integrands share a launch, or on how
  * work is split between launches.
@@ -121,8 +122,9 @@ typedef struct zmc_options {
                                     on a slice of a new plan's work (or reuse the
                                     cache); never changes results                   */
     int32_t device;              /* CUDA device ordinal                              */
-    uint32_t quads_per_lane;     /* chunk = 128 * quads_per_lane samples; 0 -> 64,
-                                    or 32 when serving is set.
+    uint32_t quints_per_lane;    /* chunk = 160 * quints_per_lane samples (a quint
+                                    is 5 consecutive samples); 0 -> 52, or 26 when
+                                    serving is set.
                                     Results are bit-identical for a fixed value and
                                     agree within rounding across values.            */
     const char *tune_cache_path; /* autotune JSON cache; NULL -> no file             */
@@ -139,7 +141,7 @@ typedef struct zmc_plan_info {
     uint64_t n_samples;    /* total samples over all integrands                    */
     uint32_t grid;         /* largest persistent grid over the family kernels      */
     uint32_t block;        /* default threads per block                            */
-    uint32_t quads_per_lane;
+    uint32_t quints_per_lane;
     uint32_t sms;
     uint32_t family_grid[4];   /* per family kernel (harmonic, abs-linear, Gaussian, */
     uint32_t family_block[4];  /* polynomial); block 0 = family absent             */
@@ -183,13 +185,13 @@ zmc_status zmc_integrate_plain(zmc_ctx *ctx, const zmc_desc *desc, size_t n,
                                zmc_result *out);
 
 /* Moments of desc[i]'s integrand over samples [s_begin[i], s_end[i]) of its
- * stream (host arrays; s_begin a multiple of 4, s_begin < s_end; desc[i].n_samples
+ * stream (host arrays; s_begin a multiple of 5, s_begin < s_end; desc[i].n_samples
  * is ignored).  Because every sample is addressed by its Philox counter, pieces
  * of one stream combine exactly: for pieces a, b with d = mean_b - mean_a,
  *     n = n_a + n_b,  mean = mean_a + d n_b / n,  M2 = M2_a + M2_b + d^2 n_a n_b / n
  * (Chan et al.), and estimate = V mean, stderr = V sqrt(M2 / (n (n-1))) of the
  * merged moments give zmc_integrate's result for the union of the pieces (equal up
- * to FP64 rounding; chunk-aligned boundaries, multiples of 128 * quads_per_lane,
+ * to FP64 rounding; chunk-aligned boundaries, multiples of 160 * quints_per_lane,
  * reproduce the same FP32 chunk sums).  This is how one stream is split over
  * GPUs or processes, checkpointed between pieces, or extended to more samples
  * later.  Blocking, like zmc_integrate. */
@@ -234,7 +236,7 @@ zmc_status zmc_cancel(zmc_ctx *ctx, uint64_t job_id);
  * stops receiving chunks at once; when the chunks already in flight have
  * finished, out[i] (n entries, host) holds the moments of every sample integrand
  * i has taken so far -- the first out[i].n samples of its stream, a multiple of
- * 128 * quads_per_lane unless the integrand is complete -- including the moments
+ * 160 * quints_per_lane unless the integrand is complete -- including the moments
  * it was resumed from.  A queued job is released at once with its starting
  * moments (n = 0 for a fresh job).  Samples are addressed by their Philox
  * counter (Sec. "Solution method": direct MC per integrand; the generator is
@@ -251,7 +253,7 @@ zmc_status zmc_checkpoint(zmc_ctx *ctx, uint64_t job_id, zmc_moments *out, int32
  * integrand i samples [from[i].n, desc[i].n_samples) of its stream and its
  * result combines from[i] with them (Chan's pairwise update on the device), so
  * that it equals an uninterrupted run of desc[i] up to FP64 rounding of the
- * merge.  Needs from[i].n <= desc[i].n_samples and from[i].n a multiple of 4 or
+ * merge.  Needs from[i].n <= desc[i].n_samples and from[i].n a multiple of 5 or
  * equal to n_samples (ZMC_EINVAL otherwise); from[i].n = 0 starts afresh.
  * Otherwise as zmc_submit. */
 zmc_status zmc_submit_resume(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *from,
@@ -302,7 +304,7 @@ zmc_status zmc_philox4x32_10(zmc_ctx *ctx, const uint32_t *ctr, const uint32_t *
  * thread), timed with CUDA events on the context's stream after one untimed
  * launch.  n_blocks (1..2^40) is rounded up to a whole number of groups of 4
  * per thread.  The paper has no counterpart; it measures the ceiling of every
- * sampling kernel, which draws d / 4 blocks per d-dimensional sample.
+ * sampling kernel, which draws d / 5 blocks per d-dimensional sample.
  * ZMC_EINVAL for n_blocks out of range, ZMC_ENOMEM if the arena cannot hold
  * one word per thread, ZMC_ECUDA on a CUDA error. */
 zmc_status zmc_philox_rate(zmc_ctx *ctx, uint64_t n_blocks, double *blocks_per_second);
@@ -446,14 +448,14 @@ zmc_status zmc_normal_integrate_udf(zmc_ctx *ctx, const zmc_udf *udf, const doub
  * ZMC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.
  *   - At most ZMC_NOALLOC_MAX_FNS integrands (ZMC_EINVAL beyond) and at most
- *     ~1.6e10 samples in total at 8192 samples per chunk (ZMC_ENOMEM beyond, with
+ *     ~1.6e10 samples in total at 8320 samples per chunk (ZMC_ENOMEM beyond, with
  *     the needed size in zmc_last_error()).
  *   - All calls share the array and it keeps the previous call's contents; each
  *     call re-uploads its tables and zeroes its work counters.  Calls whose GPU
  *     work overlaps (other streams, or unordered host threads) race: order them.
  *   - The first call on a device looks up the array's device address with that
  *     device current; make it before any stream capture.
- *   - Results equal zmc_integrate's with the default quads_per_lane (64).      */
+ *   - Results equal zmc_integrate's with the default quints_per_lane (52).      */
 #define ZMC_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define ZMC_NOALLOC_MAX_FNS 4096u
 zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_result *out,

@@ -108,7 +108,7 @@ class Oracle:
         return out
 
     def samples(self, row, s_begin: int, count: int):
-        """Raw Philox words, points and values of samples [s_begin, s_begin+count)."""
+        """Raw 23-bit fields, points and values of samples [s_begin, s_begin+count)."""
         d = int(row["dim"])
         words = np.zeros((count, d), dtype=np.uint32)
         x = np.zeros((count, d))

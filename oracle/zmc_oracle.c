@@ -22,15 +22,17 @@
  *   for the spread of one run).  mean and M2 are accumulated with Welford's
  *   one-sample update in FP64, in sample order.
  *
- *   Sampling: integrand f (key = seed, stream = stream_id) consumes the word
- *   stream w = s*d + i (sample s, coordinate i).  Word w is lane (w mod 4) of
- *   Philox4x32-10 applied to counter (stream_id, b mod 2^32, b div 2^32, 0)
- *   with key (seed mod 2^32, seed div 2^32), b = w div 4.  Philox4x32-10 is
- *   the generator of Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
- *   as easy as 1, 2, 3" (SC'11): ten rounds of the 4x32 S-box with the two
- *   published multipliers, the key bumped by the two published Weyl constants
- *   between rounds.  The 23 low bits of a word give u = (r & 0x7FFFFF) * 2^-23
- *   in [0, 1), exact in binary64, and x_i = lo_i + (hi_i - lo_i) * u_i.
+ *   Sampling: integrand f (key = seed, stream = stream_id) consumes the field
+ *   stream c = s*d + i (sample s, coordinate i).  Field c is the 23-bit field
+ *   k = c mod 5, bits 23k .. 23k+22, of block b = c div 5, where a block is the
+ *   128-bit output of Philox4x32-10 applied to counter (stream_id, b mod 2^32,
+ *   b div 2^32, 0) with key (seed mod 2^32, seed div 2^32), read as one number
+ *   with its word 0 least significant (five fields per block; its top 13 bits
+ *   are not used).  Philox4x32-10 is the generator of Salmon, Moraes, Dror and
+ *   Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten rounds of
+ *   the 4x32 S-box with the two published multipliers, the key bumped by the
+ *   two published Weyl constants between rounds.  A field r gives
+ *   u = r * 2^-23 in [0, 1), exact in binary64, and x_i = lo_i + (hi_i - lo_i) u_i.
  *
  *   Integrand families, evaluated directly in FP64 with libm:
  *     HARMONIC  a cos(k.x) + b sin(k.x)                      (Eq. 1)
@@ -110,16 +112,16 @@ typedef struct {
     const double *lo, *hi, *p;
 } zo_fn;
 
-/* Word w of an integrand's stream, with a one-block cache (w increases). */
+/* Field c of an integrand's stream, with a one-block cache (c increases). */
 typedef struct {
     uint64_t block;
     int valid;
     uint32_t words[4];
 } zo_cache;
 
-static uint32_t zo_word(const zo_fn *f, uint64_t w, zo_cache *cache)
+static uint32_t zo_field(const zo_fn *f, uint64_t c, zo_cache *cache)
 {
-    uint64_t b = w >> 2;
+    uint64_t b = c / 5;
     if (!cache->valid || cache->block != b) {
         uint32_t ctr[4] = {f->stream_id, (uint32_t)b, (uint32_t)(b >> 32), 0u};
         uint32_t key[2] = {(uint32_t)f->seed, (uint32_t)(f->seed >> 32)};
@@ -127,7 +129,15 @@ static uint32_t zo_word(const zo_fn *f, uint64_t w, zo_cache *cache)
         cache->block = b;
         cache->valid = 1;
     }
-    return cache->words[w & 3u];
+    /* bits 23k .. 23k+22 of the block, one bit at a time: block bit q is bit
+       q mod 32 of word q div 32 */
+    uint32_t first = 23u * (uint32_t)(c % 5);
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < 23; ++j) {
+        uint32_t q = first + j;
+        r |= ((cache->words[q / 32] >> (q % 32)) & 1u) << j;
+    }
+    return r;
 }
 
 static double zo_uniform(uint32_t r)
@@ -177,11 +187,11 @@ static double zo_eval(const zo_fn *f, const double *x)
     }
 }
 
-/* Point x of sample s (and its d raw words). */
+/* Point x of sample s (and its d raw 23-bit fields). */
 static void zo_point(const zo_fn *f, uint64_t s, zo_cache *cache, uint32_t *words, double *x)
 {
     for (uint32_t i = 0; i < f->dim; ++i) {
-        uint32_t r = zo_word(f, s * (uint64_t)f->dim + i, cache);
+        uint32_t r = zo_field(f, s * (uint64_t)f->dim + i, cache);
         if (words)
             words[i] = r;
         x[i] = f->lo[i] + (f->hi[i] - f->lo[i]) * zo_uniform(r);
@@ -278,7 +288,7 @@ void zo_moments(uint32_t family, uint32_t dim, uint32_t stream_id, uint32_t deg,
     zo_moments_fn(&f, s_begin, s_end, &out4[0], &out4[1], &out4[2], &out4[3]);
 }
 
-/* Raw words (count x dim), points (count x dim) and values (count) of samples
+/* Raw 23-bit fields (count x dim), points (count x dim) and values (count) of samples
  * [s_begin, s_begin + count) of one integrand. */
 void zo_samples(uint32_t family, uint32_t dim, uint32_t stream_id, uint32_t deg,
                 uint64_t seed, const double *lo, const double *hi, const double *p,

@@ -138,53 +138,53 @@ __device__ __forceinline__ uint4 philox_block(uint32_t block_lo, const StreamPre
   return make_uint4(c0, c1, c2, c3);
 }
 
-// The 4*D words of one quad (4 consecutive samples starting at a multiple of 4):
-// sample t, coordinate i is word t*D + i, i.e. lane (t*D+i)%4 of Philox block
-// quad*D + (t*D+i)/4.
+// The five 23-bit fields of one Philox block: field k is bits [23k, 23k + 23) of
+// the 128-bit output (word 0 least significant), delivered in the low 23 bits
+// of f[k]; the bits above are not part of the field, and every consumer masks
+// with 0x7FFFFF.  13 of the 128 bits go unused.
+__device__ __forceinline__ void block_fields(const uint4 o, uint32_t *f) {
+  f[0] = o.x;
+  f[1] = __funnelshift_r(o.x, o.y, 23);
+  f[2] = __funnelshift_r(o.y, o.z, 14);
+  f[3] = o.z >> 5;
+  f[4] = __funnelshift_r(o.z, o.w, 28);
+}
+
+// The 5*D fields of one quint (5 consecutive samples starting at a multiple of
+// 5): sample t, coordinate i is field t*D + i, i.e. field (t*D+i)%5 of Philox
+// block quint*D + (t*D+i)/5.
 template <int D>
-__device__ __forceinline__ void gen_quad(uint64_t quad, uint32_t sid, const RoundKeys &rk,
-                                         uint32_t (&r)[4 * D]) {
+__device__ __forceinline__ void gen_quint(uint64_t quint, uint32_t sid, const RoundKeys &rk,
+                                          uint32_t (&r)[5 * D]) {
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    const uint64_t b = quad * D + static_cast<uint64_t>(j);
-    const uint4 o = philox(sid, static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), 0u, rk);
-    r[4 * j + 0] = o.x;
-    r[4 * j + 1] = o.y;
-    r[4 * j + 2] = o.z;
-    r[4 * j + 3] = o.w;
+    const uint64_t b = quint * D + static_cast<uint64_t>(j);
+    block_fields(philox(sid, static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), 0u, rk),
+                 r + 5 * j);
   }
 }
 
-// The same words by way of the chunk prefix, made here for every block (the
+// The same fields by way of the chunk prefix, made here for every block (the
 // per-sample test path, which thereby checks philox_block for any block hi).
 template <int D>
-__device__ __forceinline__ void gen_quad_prefixed(uint64_t quad, uint32_t sid,
-                                                  const RoundKeys &rk, uint32_t (&r)[4 * D]) {
+__device__ __forceinline__ void gen_quint_prefixed(uint64_t quint, uint32_t sid,
+                                                   const RoundKeys &rk, uint32_t (&r)[5 * D]) {
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    const uint64_t b = quad * D + static_cast<uint64_t>(j);
+    const uint64_t b = quint * D + static_cast<uint64_t>(j);
     const StreamPrefix sp = make_stream_prefix(rk, sid, static_cast<uint32_t>(b >> 32));
-    const uint4 o = philox_block(static_cast<uint32_t>(b), sp);
-    r[4 * j + 0] = o.x;
-    r[4 * j + 1] = o.y;
-    r[4 * j + 2] = o.z;
-    r[4 * j + 3] = o.w;
+    block_fields(philox_block(static_cast<uint32_t>(b), sp), r + 5 * j);
   }
 }
 
-// The same words when the caller guarantees that the block index's high word is
-// the one the prefix was made for: base_lo is the low word of block quad*D.
+// The same fields when the caller guarantees that the block index's high word
+// is the one the prefix was made for: base_lo is the low word of block quint*D.
 template <int D>
-__device__ __forceinline__ void gen_quad_fast(uint32_t base_lo, const StreamPrefix &sp,
-                                              uint32_t (&r)[4 * D]) {
+__device__ __forceinline__ void gen_quint_fast(uint32_t base_lo, const StreamPrefix &sp,
+                                               uint32_t (&r)[5 * D]) {
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    const uint4 o = philox_block(base_lo + static_cast<uint32_t>(j), sp);
-    r[4 * j + 0] = o.x;
-    r[4 * j + 1] = o.y;
-    r[4 * j + 2] = o.z;
-    r[4 * j + 3] = o.w;
-  }
+  for (int j = 0; j < D; ++j)
+    block_fields(philox_block(base_lo + static_cast<uint32_t>(j), sp), r + 5 * j);
 }
 
 __device__ __forceinline__ float unit_v(uint32_t word) {
@@ -194,8 +194,9 @@ __device__ __forceinline__ float unit_v(uint32_t word) {
 
 // ---------------------------------------------------------------- integrands (FP32)
 // Eval<FAM, D, G>: load(fn) reads the integrand's FP32 constants from FnDev;
-// operator()(r) returns the scaled value f' = S f at the sample whose D Philox
-// words are r[0..D).  Specialised per family in zmc_fam_<family>.cu.
+// operator()(r) returns the scaled value f' = S f at the sample whose D 23-bit
+// fields are the low 23 bits of r[0..D).  Specialised per family in
+// zmc_fam_<family>.cu.
 template <int FAM, int D, int G>
 struct Eval;
 
@@ -226,30 +227,31 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
   return v;
 }
 
-// Samples [chunk * 128Q, min(+128Q, N)) of one integrand.  Lane l takes quads
-// l, l+32, ..., l+32(Q-1) of the chunk.  Over each block of kBlockQuads of its
-// quads it accumulates in FP32
-//   s1 = sum f            (each quad summed pairwise first; unshifted, so its
+// Samples [chunk * 160Q, min(+160Q, N)) of one integrand.  Lane l takes quints
+// l, l+32, ..., l+32(Q-1) of the chunk.  Over each block of kBlockQuints of its
+// quints it accumulates in FP32
+//   s1 = sum f            (each quint summed pairwise first; unshifted, so its
 //                          rounding error scales with the values themselves)
 //   s2 = sum (f - K)^2    (K = the block's first value, so that s2 does not hold
 //                          mean^2 n when the spread is small)
 // turns them into (n, mean = s1/n, M2 = s2 - n (mean - K)^2) and merges that into
 // the lane's running summary (Chan's pairwise update); the warp then merges the
 // 32 lane summaries the same way.
-// Quads of one lane interleaved per loop step, per family (build-time knobs).
-#ifndef ZMC_QUAD_UNROLL
-#define ZMC_QUAD_UNROLL 1
+// Quints of one lane interleaved per loop step, per family (build-time knobs).
+#ifndef ZMC_QUINT_UNROLL
+#define ZMC_QUINT_UNROLL 1
 #endif
-#ifndef ZMC_QUAD_UNROLL_HARMONIC
-#define ZMC_QUAD_UNROLL_HARMONIC ZMC_QUAD_UNROLL
+#ifndef ZMC_QUINT_UNROLL_HARMONIC
+#define ZMC_QUINT_UNROLL_HARMONIC ZMC_QUINT_UNROLL
 #endif
 template <int FAM>
-struct QuadUnroll {
-  static constexpr int value = FAM == ZMC_HARMONIC ? ZMC_QUAD_UNROLL_HARMONIC : ZMC_QUAD_UNROLL;
+struct QuintUnroll {
+  static constexpr int value =
+      FAM == ZMC_HARMONIC ? ZMC_QUINT_UNROLL_HARMONIC : ZMC_QUINT_UNROLL;
 };
-// Quads per accumulation block: a lane's shifted sums never span more than
-// 4 * kBlockQuads samples, which bounds their rounding error for any chunk length.
-constexpr uint32_t kBlockQuads = 16;
+// Quints per accumulation block: a lane's shifted sums never span more than
+// 5 * kBlockQuints samples, which bounds their rounding error for any chunk length.
+constexpr uint32_t kBlockQuints = 13;
 template <int FAM, int D, int G, bool FAST>
 __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t chunk,
                                           uint32_t Q, uint32_t lane) {
@@ -257,55 +259,55 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
   ev.load(fn);
   const RoundKeys rk = make_round_keys(fn->key0, fn->key1);
   const uint32_t sid = fn->stream_id;
-  const uint64_t chunk_samples = 128ull * Q;
+  const uint64_t chunk_samples = chunk_samples_of(Q);
   const uint64_t s0 = chunk * chunk_samples;
   const uint64_t n_left = fn->n_samples - s0;
   const uint32_t nc = static_cast<uint32_t>(n_left < chunk_samples ? n_left : chunk_samples);
-  const uint64_t quad0 = (fn->s_off + s0) >> 2;  // s_off is a multiple of 4
-  const uint64_t block0 = quad0 * D;
+  const uint64_t quint0 = (fn->s_off + s0) / kQuint;  // s_off is a multiple of 5
+  const uint64_t block0 = quint0 * D;
   const uint32_t base_lo0 = static_cast<uint32_t>(block0) + lane * D;
   const StreamPrefix sp = make_stream_prefix(rk, sid, static_cast<uint32_t>(block0 >> 32));
 
-  // running (n, mean, M2) of the lane, merged from blocks of kBlockQuads quads
+  // running (n, mean, M2) of the lane, merged from blocks of kBlockQuints quints
   float n = 0.0f, mean = 0.0f, m2 = 0.0f;
-  for (uint32_t jb = 0; jb < Q; jb += kBlockQuads) {
-    const uint32_t je = jb + kBlockQuads < Q ? jb + kBlockQuads : Q;
+  for (uint32_t jb = 0; jb < Q; jb += kBlockQuints) {
+    const uint32_t je = jb + kBlockQuints < Q ? jb + kBlockQuints : Q;
     float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
     uint32_t cnt = 0;
-#pragma unroll QuadUnroll<FAM>::value
+#pragma unroll QuintUnroll<FAM>::value
     for (uint32_t j = jb; j < je; ++j) {
       const uint32_t ql = lane + 32u * j;
-      if (!FAST && 4u * ql >= nc) break;
-      uint32_t r[4 * D];
+      if (!FAST && kQuint * ql >= nc) break;
+      uint32_t r[5 * D];
       if (FAST)
-        gen_quad_fast<D>(base_lo0 + 32u * D * j, sp, r);
+        gen_quint_fast<D>(base_lo0 + 32u * D * j, sp, r);
       else
-        gen_quad<D>(quad0 + ql, sid, rk, r);
-      float f[4];
+        gen_quint<D>(quint0 + ql, sid, rk, r);
+      float f[5];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) f[t] = ev(r + t * D);
+      for (int t = 0; t < 5; ++t) f[t] = ev(r + t * D);
       if (j == jb) K = f[0];
       if (FAST) {
-        s1 += (f[0] + f[1]) + (f[2] + f[3]);
+        s1 += ((f[0] + f[1]) + (f[2] + f[3])) + f[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < 5; ++t) {
           const float dlt = f[t] - K;
           s2 = fmaf(dlt, dlt, s2);
         }
       } else {
-        float q[4];
+        float q[5];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const bool ok = 4u * ql + t < nc;
+        for (int t = 0; t < 5; ++t) {
+          const bool ok = kQuint * ql + t < nc;
           q[t] = ok ? f[t] : 0.0f;
           const float dlt = ok ? f[t] - K : 0.0f;
           s2 = fmaf(dlt, dlt, s2);
           cnt += ok ? 1u : 0u;
         }
-        s1 += (q[0] + q[1]) + (q[2] + q[3]);
+        s1 += ((q[0] + q[1]) + (q[2] + q[3])) + q[4];
       }
     }
-    const float nb = FAST ? static_cast<float>(4u * (je - jb)) : static_cast<float>(cnt);
+    const float nb = FAST ? static_cast<float>(kQuint * (je - jb)) : static_cast<float>(cnt);
     if (nb > 0.0f) {
       const float mb = __fdiv_rn(s1, nb);
       const float dk = mb - K;
@@ -317,7 +319,7 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
       m2 = m2 + m2b + delta * delta * (n * wb);
       n = nab;
     }
-    if (!FAST && cnt < 4u * (je - jb)) break;
+    if (!FAST && cnt < kQuint * (je - jb)) break;
   }
   warp_chan_merge(n, mean, m2);
   if (lane == 0) fn->rec[chunk] = make_float2(mean, m2);
@@ -326,11 +328,11 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
 template <int FAM, int D, int G>
 __device__ __forceinline__ void run_item(const FnDev *__restrict__ fn, uint64_t chunk,
                                          uint32_t Q, uint32_t lane) {
-  const uint64_t chunk_samples = 128ull * Q;
+  const uint64_t chunk_samples = chunk_samples_of(Q);
   const uint64_t s0 = chunk * chunk_samples;
   const bool full = fn->n_samples - s0 >= chunk_samples;
-  const uint64_t b_first = ((fn->s_off + s0) >> 2) * D;
-  const uint64_t b_last = b_first + (chunk_samples >> 2) * D - 1;
+  const uint64_t b_first = ((fn->s_off + s0) / kQuint) * D;
+  const uint64_t b_last = b_first + (chunk_samples / kQuint) * D - 1;
   if (full && (b_first >> 32) == (b_last >> 32))
     run_chunk<FAM, D, G, true>(fn, chunk, Q, lane);
   else
@@ -440,7 +442,7 @@ __device__ __forceinline__ void batched_loop(const Entry *__restrict__ entries,
   const unsigned long long begin = hdr->item_begin[kSlot];
   const unsigned long long count = hdr->item_end[kSlot] - begin;
   const uint32_t ne = hdr->n_entries;
-  const uint32_t Q = hdr->quads_per_lane;
+  const uint32_t Q = hdr->quints_per_lane;
   uint32_t e = 0;
   for (;;) {
     unsigned long long k = 0;
@@ -469,15 +471,15 @@ __device__ __forceinline__ void eval_range(const FnDev *fn, uint64_t s_begin, ui
   Eval<FAM, D, G> ev;
   ev.load(fn);
   const RoundKeys rk = make_round_keys(fn->key0, fn->key1);
-  const uint64_t q_first = s_begin >> 2;
-  const uint64_t q_last = (s_begin + count - 1) >> 2;
+  const uint64_t q_first = s_begin / kQuint;
+  const uint64_t q_last = (s_begin + count - 1) / kQuint;
   for (uint64_t q = q_first + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
        q <= q_last; q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-    uint32_t r[4 * D];
-    gen_quad_prefixed<D>(q, fn->stream_id, rk, r);
+    uint32_t r[5 * D];
+    gen_quint_prefixed<D>(q, fn->stream_id, rk, r);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const uint64_t s = 4 * q + t;
+    for (int t = 0; t < 5; ++t) {
+      const uint64_t s = kQuint * q + t;
       if (s >= s_begin && s < s_begin + count)
         out[s - s_begin] = static_cast<float>(static_cast<double>(ev(r + t * D)) * fn->inv_scale);
     }
@@ -520,8 +522,8 @@ template <int FAM>
 cudaError_t launch_eval_family(const FnDev *fn, uint64_t s_begin, uint32_t count, float *out,
                                cudaStream_t stream) {
   if (count == 0) return cudaSuccess;
-  const uint64_t quads = ((s_begin + count - 1) >> 2) - (s_begin >> 2) + 1;
-  const uint64_t blocks = (quads + 255) / 256;
+  const uint64_t quints = (s_begin + count - 1) / kQuint - s_begin / kQuint + 1;
+  const uint64_t blocks = (quints + 255) / 256;
   zmc_eval_kernel<FAM><<<static_cast<unsigned>(blocks < 1024 ? blocks : 1024), 256, 0, stream>>>(
       fn, s_begin, count, out);
   return cudaGetLastError();

@@ -21,6 +21,14 @@ namespace zmc {
 constexpr int kMaxDim = 7;
 constexpr int kWarp = 32;
 
+// A lane's unit of work is a quint: 5 consecutive samples (starting at a multiple
+// of 5) whose 5 D coordinates are the 5 D 23-bit fields of D Philox blocks (five
+// fields per 128-bit block).  A chunk is 32 lanes x quints_per_lane quints.
+constexpr uint32_t kQuint = 5;
+__host__ __device__ constexpr uint64_t chunk_samples_of(uint32_t quints_per_lane) {
+  return 32ull * kQuint * quints_per_lane;
+}
+
 // Variant code: dimension in bits 0..3 (1..12), family in bits 4..6, and in
 // bits 8 and up the polynomial's variant degree (0..7) or the index of a user
 // function in its module (0..63).  The sampling kernel dispatches one
@@ -71,7 +79,7 @@ struct alignas(16) FnDev {
   zmc_result *out;    // result row written by the merge kernel
   double volume;      // prod (hi_i - lo_i), FP64
   double inv_scale;   // 1 / S (a power of two)
-  uint64_t s_off;     // absolute index of sample 0 (a multiple of 4): sample s of
+  uint64_t s_off;     // absolute index of sample 0 (a multiple of 5): sample s of
                       // this descriptor is sample s_off + s of the Philox stream
   uint32_t w[72];
   // Moments (unscaled) of samples taken before this descriptor's, e.g. a
@@ -103,7 +111,7 @@ struct LaunchHdr {
   unsigned long long item_end[4];
   uint32_t n_entries;
   uint32_t n_merge;                  // integrands to merge after this launch
-  uint32_t quads_per_lane;           // chunk = 128 * quads_per_lane samples
+  uint32_t quints_per_lane;          // chunk = 160 * quints_per_lane samples
   uint32_t pad;
 };
 

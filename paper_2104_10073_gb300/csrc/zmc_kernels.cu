@@ -15,13 +15,13 @@
 //                        with its spread).
 //   zmc_plain_fp64_kernel  (zmc_plain.cu) the plain form, one launch per integrand.
 //   zmc_philox_rate_kernel  the generator alone (its throughput: the ceiling of
-//                        any sampling kernel, which draws d / 4 blocks per sample).
+//                        any sampling kernel, which draws d / 5 blocks per sample).
 //   zmc_philox_kernel, zmc_eval_kernel<FAM>   the generator and the per-sample
 //                        integrand values of the sampling path, for parity tests.
 //
 // No tensor cores and no TMA: the path is integer and FP32 arithmetic on the FMA,
 // ALU and MUFU pipes, with a few KB of descriptor reads and 8 bytes written per
-// 128 * quads_per_lane samples.
+// 160 * quints_per_lane samples.
 #include "zmc_device.cuh"
 
 namespace zmc {
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) zmc_merge_kernel(const FnDev *const *__re
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t nm = hdr->n_merge;
-  const uint64_t chunk_samples = 128ull * hdr->quads_per_lane;
+  const uint64_t chunk_samples = chunk_samples_of(hdr->quints_per_lane);
   for (uint32_t k = warp; k < nm; k += nwarps) {
     const FnDev *fn = fns[k];
     const uint64_t N = fn->n_samples;

@@ -35,7 +35,7 @@ namespace {
 
 constexpr size_t kScratchBytes = ZMC_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kMaxFns = ZMC_NOALLOC_MAX_FNS;
-constexpr uint32_t kQuads = 64;  // the default chunk, so results equal zmc_integrate's
+constexpr uint32_t kQuints = 52;  // the default chunk, so results equal zmc_integrate's
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -82,7 +82,7 @@ extern "C" zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_
   const size_t off_mrg = kOffEnt + r256(n * sizeof(Entry));
   const size_t off_fns = off_mrg + r256(n * sizeof(const FnDev *));
   const size_t off_rec = off_fns + r256(n * sizeof(FnDev));
-  const uint64_t chunk = 128ull * kQuads;
+  const uint64_t chunk = chunk_samples_of(kQuints);
   uint64_t chunks = 0;
   for (size_t i = 0; i < n; ++i) {
     if (desc[i].n_samples == 0 || desc[i].n_samples > (1ull << 62))
@@ -142,7 +142,7 @@ extern "C" zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_
   }
   hdr->n_entries = static_cast<uint32_t>(n);
   hdr->n_merge = static_cast<uint32_t>(n);
-  hdr->quads_per_lane = kQuads;
+  hdr->quints_per_lane = kQuints;
 
   // launch shape: the persistent grid of each family kernel on this device
   int sms = 0;

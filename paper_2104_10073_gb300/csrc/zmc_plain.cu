@@ -1,7 +1,7 @@
 // zmc_plain.cu -- the plain FP64 form: one direct-MC launch per integrand
 // (FP64 map and evaluation with the CUDA math library, FP64 block reductions of
 // (n, mean, M2)), then one merge launch for all integrands.  The baseline the
-// batched FP32 path is measured against; same generator and word layout.
+// batched FP32 path is measured against; same generator and field layout.
 #include "zmc_device.cuh"
 
 namespace zmc {
@@ -38,22 +38,22 @@ __device__ __forceinline__ double eval_f64(const PlainFn &fn, const double *x, i
   }
 }
 
-// One thread per quad (grid-stride); per-thread FP64 shifted sums; block-level
+// One thread per quint (grid-stride); per-thread FP64 shifted sums; block-level
 // Chan merge in shared memory; one (n, mean, M2) record per block.
 template <int FAM, int D>
 __global__ void __launch_bounds__(256) zmc_plain_fp64_kernel(const PlainFn fn,
                                                              double *__restrict__ rec) {
   const RoundKeys rk = make_round_keys(fn.key0, fn.key1);
   const uint64_t N = fn.n_samples;
-  const uint64_t nquads = (N + 3) / 4;
+  const uint64_t nquints = (N + kQuint - 1) / kQuint;
   double K = 0.0, s1 = 0.0, s2 = 0.0, cnt = 0.0;
-  for (uint64_t q = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; q < nquads;
+  for (uint64_t q = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; q < nquints;
        q += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-    uint32_t r[4 * D];
-    gen_quad<D>(q, fn.stream_id, rk, r);
+    uint32_t r[5 * D];
+    gen_quint<D>(q, fn.stream_id, rk, r);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (4 * q + t < N) {
+    for (int t = 0; t < 5; ++t) {
+      if (kQuint * q + t < N) {
         double x[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
@@ -132,8 +132,8 @@ __global__ void zmc_plain_merge_kernel(const PlainJob *__restrict__ jobs, uint32
 }  // namespace
 
 unsigned plain_grid(const PlainFn &fn, int sms) {
-  const uint64_t nquads = (fn.n_samples + 3) / 4;
-  const uint64_t want = (nquads + 255) / 256;
+  const uint64_t nquints = (fn.n_samples + kQuint - 1) / kQuint;
+  const uint64_t want = (nquints + 255) / 256;
   const uint64_t cap = static_cast<uint64_t>(sms) * 8;
   return static_cast<unsigned>(want < cap ? (want > 0 ? want : 1) : cap);
 }

@@ -587,9 +587,10 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
     }
     len[i] = desc[i].n_samples;
     if (s_begin) {
-      if (s_begin[i] % 4 != 0 || !(s_end[i] > s_begin[i]) || s_end[i] - s_begin[i] > (1ull << 62))
+      if (s_begin[i] % kQuint != 0 || !(s_end[i] > s_begin[i]) ||
+          s_end[i] - s_begin[i] > (1ull << 62))
         return set_error(ZMC_EINVAL,
-                         "range %zu: need s_begin a multiple of 4 and s_begin < s_end", i);
+                         "range %zu: need s_begin a multiple of 5 and s_begin < s_end", i);
       if (s_end[i] > ~0ull / kMaxDim)
         return set_error(ZMC_EINVAL, "range %zu: sample index too large", i);
       fns[i].s_off = s_begin[i];
@@ -598,7 +599,7 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
       fns[i].out_mode = 1;
     }
   }
-  const uint64_t chunk = 128ull * ctx->quads_per_lane;
+  const uint64_t chunk = chunk_samples_of(ctx->quints_per_lane);
   std::vector<uint64_t> nchunk(n), rec_off(n);
   uint64_t total = 0, samples = 0;
   for (size_t i = 0; i < n; ++i) {
@@ -665,7 +666,7 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
   }
   h.n_entries = static_cast<uint32_t>(n);
   h.n_merge = static_cast<uint32_t>(n);
-  h.quads_per_lane = ctx->quads_per_lane;
+  h.quints_per_lane = ctx->quints_per_lane;
   for (int f = 0; f < 4; ++f) {
     plan->fam_items[f] = h.item_end[f] - h.item_begin[f];
     plan->block[f] = ctx->shape.block;
@@ -816,7 +817,7 @@ zmc_status zmc_default_options(zmc_options *opt) {
   if (!opt) return set_error(ZMC_EINVAL, "null options");
   std::memset(opt, 0, sizeof *opt);
   opt->mem_budget_bytes = 1ull << 30;
-  opt->quads_per_lane = 0;  // chosen at zmc_create
+  opt->quints_per_lane = 0;  // chosen at zmc_create
   return ZMC_OK;
 }
 
@@ -852,8 +853,8 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   // longer chunks amortise the per-chunk work (keys, descriptor loads, warp
   // merge: 8192 samples measured fastest for whole tables); serving keeps them
   // at 4096, which measured lower job latency under load
-  if (opt.quads_per_lane == 0) opt.quads_per_lane = opt.serving ? 32 : 64;
-  if (opt.quads_per_lane > 1024) return set_error(ZMC_EINVAL, "quads_per_lane above 1024");
+  if (opt.quints_per_lane == 0) opt.quints_per_lane = opt.serving ? 26 : 52;
+  if (opt.quints_per_lane > 1024) return set_error(ZMC_EINVAL, "quints_per_lane above 1024");
   if (opt.arena && (reinterpret_cast<uintptr_t>(opt.arena) & 255))
     return set_error(ZMC_EINVAL, "arena must be 256-byte aligned");
   int ndev = 0;
@@ -891,7 +892,7 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
     ctx->own_arena = true;
   }
   ctx->arena.init(ctx->arena_base, opt.mem_budget_bytes);
-  ctx->quads_per_lane = opt.quads_per_lane;
+  ctx->quints_per_lane = opt.quints_per_lane;
   ctx->max_chunks_per_iter = opt.max_chunks_per_iter;
   ctx->autotune = opt.autotune != 0;
   if (opt.tune_cache_path) ctx->tune_cache_path = opt.tune_cache_path;
@@ -1005,7 +1006,7 @@ zmc_status zmc_plan_info_get(const zmc_plan *plan, zmc_plan_info *out) {
     out->family_block[f] = plan->fam_items[f] ? plan->block[f] : 0;
     out->tune_source[f] = plan->tune_source[f];
   }
-  out->quads_per_lane = plan->ctx->quads_per_lane;
+  out->quints_per_lane = plan->ctx->quints_per_lane;
   out->sms = static_cast<uint32_t>(plan->ctx->sms);
   return ZMC_OK;
 }

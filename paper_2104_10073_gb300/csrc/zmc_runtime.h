@@ -98,7 +98,7 @@ struct zmc_ctx {
   char *arena_base = nullptr;
   bool own_arena = false;
   zmc::Arena arena;
-  uint32_t quads_per_lane = 16;
+  uint32_t quints_per_lane = 16;
   uint32_t max_chunks_per_iter = 0;
   bool autotune = false;
   std::string tune_cache_path;

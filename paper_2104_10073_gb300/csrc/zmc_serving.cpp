@@ -424,7 +424,7 @@ void scheduler_loop(ServingState *S) {
       hdr->item_end[f] = item;
     }
     hdr->n_entries = k;
-    hdr->quads_per_lane = ctx->quads_per_lane;
+    hdr->quints_per_lane = ctx->quints_per_lane;
     // merge list: whole jobs whose chunks have all been issued
     uint32_t nm = 0;
     slot->finishing.clear();
@@ -453,7 +453,7 @@ void scheduler_loop(ServingState *S) {
       }
       const size_t tbytes = j->n * sizeof(FnDev);
       if (nm + j->n > S->max_merge || used + tbytes > kAdmitBytes) break;
-      const uint64_t chunk = 128ull * ctx->quads_per_lane;
+      const uint64_t chunk = chunk_samples_of(ctx->quints_per_lane);
       FnDev *cut = reinterpret_cast<FnDev *>(admit_area(S, *slot) + used);
       for (size_t i = 0; i < j->n; ++i) {
         cut[i] = j->fns[i];
@@ -533,7 +533,8 @@ zmc_status serving_start(zmc_ctx *ctx) {
   // under overload than half
   S->max_chunks = ctx->max_chunks_per_iter
                       ? ctx->max_chunks_per_iter
-                      : std::max<uint32_t>(1024, (1u << 23) / ctx->quads_per_lane);
+                      : static_cast<uint32_t>(std::max<uint64_t>(
+                            1024, (1ull << 30) / chunk_samples_of(ctx->quints_per_lane)));
   S->max_entries = std::max<uint32_t>(S->max_chunks, 1024);
   S->max_entries = std::min<uint32_t>(S->max_entries, 1u << 20);
   S->max_merge = 1u << 16;
@@ -617,7 +618,7 @@ zmc_status submit_job(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *fro
   j->family.resize(n);
   j->nchunk.resize(n);
   j->next_chunk.assign(n, 0);
-  const uint64_t chunk = 128ull * ctx->quads_per_lane;
+  const uint64_t chunk = chunk_samples_of(ctx->quints_per_lane);
   std::vector<uint8_t> ok(n, 1);
   host_parallel_for(n, 64, [&](size_t b, size_t e) {
     for (size_t i = b; i < e; ++i) ok[i] = precompute(desc[i], &j->fns[i], nullptr, nullptr) == ZMC_OK;
@@ -632,11 +633,11 @@ zmc_status submit_job(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *fro
       const zmc_moments &m = from[i];
       start = m.n;
       if (m.status != ZMC_OK || start > desc[i].n_samples ||
-          (start % 4 != 0 && start != desc[i].n_samples) || !std::isfinite(m.mean) ||
+          (start % kQuint != 0 && start != desc[i].n_samples) || !std::isfinite(m.mean) ||
           !std::isfinite(m.m2) || m.m2 < 0.0)
         return set_error(ZMC_EINVAL,
                          "descriptor %zu: resume moments need status OK, finite mean and "
-                         "M2 >= 0, n <= n_samples and n a multiple of 4 (or n_samples)", i);
+                         "M2 >= 0, n <= n_samples and n a multiple of 5 (or n_samples)", i);
       FnDev &f = j->fns[i];
       f.s_off = start;
       f.n_samples = desc[i].n_samples - start;

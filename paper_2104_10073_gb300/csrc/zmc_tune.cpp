@@ -4,12 +4,12 @@
 // The geometry decides only which warp runs which work item, never what an
 // item computes, so tuning never changes results.  Keys name what the best
 // geometry can depend on: the GPU model and SM count, the family, the chunk
-// length (quads per lane), the dominant dimension of the family's samples and
+// length (quints per lane), the dominant dimension of the family's samples and
 // the family kernel's registers per thread (its build).
 //
 // File format (written by this file only):
 //   {"version": 1, "entries": {
-//     "<gpu>|<sms>|<family>|<quads>|<dim>|r<regs>": {"block": 256, "blocks_per_sm": 2, "ms": 0.512},
+//     "<gpu>|<sms>|<family>|<quints>|<dim>|r<regs>": {"block": 256, "blocks_per_sm": 2, "ms": 0.512},
 //     ...}}
 #include <cstdio>
 #include <cstdlib>
@@ -24,7 +24,7 @@ std::string tune_key(const zmc_ctx *ctx, int family, int dim) {
   std::ostringstream k;
   // the kernel's register count stands for its build: a rebuild with other
   // launch-bound knobs is timed afresh instead of reusing another build's choice
-  k << ctx->gpu_name << '|' << ctx->sms << '|' << family << '|' << ctx->quads_per_lane << '|'
+  k << ctx->gpu_name << '|' << ctx->sms << '|' << family << '|' << ctx->quints_per_lane << '|'
     << dim << "|r" << ctx->kernel_regs[family];
   return k.str();
 }

@@ -245,7 +245,7 @@ zmc_status udf_run(zmc_ctx *ctx, const zmc_udf *udf, const UdfRow *rows, size_t 
   if (st != ZMC_OK) return st;
 
   const bool f64 = udf->precision == ZMC_UDF_F64;
-  const uint64_t chunk = 128ull * ctx->quads_per_lane;
+  const uint64_t chunk = chunk_samples_of(ctx->quints_per_lane);
   std::vector<FnDev> tab(n);
   std::vector<uint64_t> rec_off(n);
   std::vector<uint32_t> prow(n);        // FP64: index of the row's parameter block
@@ -308,7 +308,7 @@ zmc_status udf_run(zmc_ctx *ctx, const zmc_udf *udf, const UdfRow *rows, size_t 
   hdr->item_end[0] = item;
   hdr->n_entries = static_cast<uint32_t>(n);
   hdr->n_merge = static_cast<uint32_t>(n);
-  hdr->quads_per_lane = ctx->quads_per_lane;
+  hdr->quints_per_lane = ctx->quints_per_lane;
 
   cudaStream_t str = ctx->stream;
   e = cudaMemcpyAsync(d_fns, fns, fn_b, cudaMemcpyHostToDevice, str);
@@ -509,8 +509,8 @@ zmc_status zmc_udf_eval_samples(zmc_ctx *ctx, const zmc_udf *udf, const zmc_desc
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_p, s + o_p, ZMC_NPARAM * sizeof(double), cudaMemcpyHostToDevice, str);
   if (e == cudaSuccess) {
-    const uint64_t quads = ((s_begin + count - 1) >> 2) - (s_begin >> 2) + 1;
-    const unsigned grid = static_cast<unsigned>(std::min<uint64_t>((quads + 255) / 256, 1024));
+    const uint64_t quints = (s_begin + count - 1) / kQuint - s_begin / kQuint + 1;
+    const unsigned grid = static_cast<unsigned>(std::min<uint64_t>((quints + 255) / 256, 1024));
     const FnDev *a0 = d_fn;
     uint64_t a1 = s_begin;
     uint32_t a2 = count;

@@ -41,7 +41,7 @@ def partition_samples(table, world: int, align: int = 1) -> list[list[tuple[int,
     """Contiguous (row, s_begin, s_end) pieces per rank covering every sample once.
 
     Rank boundaries are rounded down to multiples of ``align`` within the global
-    sample sequence; ``align`` = the library's chunk length (128 * quads_per_lane)
+    sample sequence; ``align`` = the library's chunk length (160 * quints_per_lane)
     makes each piece start on a chunk of its row whenever rows start on one
     (pieces then reproduce the unsplit chunk sums exactly)."""
     n = [int(v) for v in table["n_samples"]]
@@ -90,7 +90,7 @@ def merge_moments(n_rows: int, pieces, volumes) -> np.ndarray:
 def rank_moments(ctx_handle: int, table, pieces) -> list[tuple[int, float, float, float]]:
     """(row, n, mean, M2) of this rank's pieces computed by the library (the
     device counterpart of the CPU oracle's moments); piece starts must be
-    multiples of 4."""
+    multiples of 5 (whole quints)."""
     from . import zmc
 
     if not pieces:

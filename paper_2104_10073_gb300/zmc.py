@@ -30,8 +30,8 @@ STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_EAGAIN",
                 8: "ZMC_ENOSYS"}
 ZMC_STAGE_SAMPLE, ZMC_STAGE_MERGE, ZMC_STAGE_ALL = 1, 2, 3
 ZMC_USER = 4
-DEFAULT_QUADS_PER_LANE = 64  # the library's default chunk: 128 x 64 = 8192 samples
-SERVING_QUADS_PER_LANE = 32  # ... and for a serving context: 4096 samples
+DEFAULT_QUINTS_PER_LANE = 52  # the library's default chunk: 160 x 52 = 8320 samples
+SERVING_QUINTS_PER_LANE = 26  # ... and for a serving context: 4160 samples
 ZMC_UDF_F32, ZMC_UDF_F64 = 0, 1
 
 RESULT_DTYPE = np.dtype([("estimate", "<f8"), ("stderr", "<f8"), ("n", "<u8"),
@@ -45,14 +45,14 @@ class zmc_options(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("arena", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("max_chunks_per_iter", ctypes.c_uint32),
                 ("autotune", ctypes.c_uint32), ("device", ctypes.c_int32),
-                ("quads_per_lane", ctypes.c_uint32), ("tune_cache_path", ctypes.c_char_p),
+                ("quints_per_lane", ctypes.c_uint32), ("tune_cache_path", ctypes.c_char_p),
                 ("serving", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class zmc_plan_info(ctypes.Structure):
     _fields_ = [("n_fn", ctypes.c_uint64), ("n_chunks", ctypes.c_uint64),
                 ("n_samples", ctypes.c_uint64), ("grid", ctypes.c_uint32),
-                ("block", ctypes.c_uint32), ("quads_per_lane", ctypes.c_uint32),
+                ("block", ctypes.c_uint32), ("quints_per_lane", ctypes.c_uint32),
                 ("sms", ctypes.c_uint32), ("family_grid", ctypes.c_uint32 * 4),
                 ("family_block", ctypes.c_uint32 * 4), ("tune_source", ctypes.c_int32 * 4)]
 
@@ -518,7 +518,7 @@ class Context:
     """
 
     def __init__(self, arena_bytes: int = 1 << 30, device: int = 0, stream=None,
-                 serving: bool = False, quads_per_lane: int = 0,
+                 serving: bool = False, quints_per_lane: int = 0,
                  max_chunks_per_iter: int = 0,
                  use_torch_memory: bool = True, autotune: bool = False,
                  tune_cache_path: str | None = None):
@@ -532,7 +532,7 @@ class Context:
         opt.device = device
         opt.stream = self.stream.cuda_stream
         opt.serving = 1 if serving else 0
-        opt.quads_per_lane = quads_per_lane
+        opt.quints_per_lane = quints_per_lane
         opt.max_chunks_per_iter = max_chunks_per_iter
         opt.autotune = 1 if autotune else 0
         self._tune_path = tune_cache_path.encode() if tune_cache_path else None

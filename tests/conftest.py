@@ -55,7 +55,7 @@ def sq_ctx(zctx):
     can be compared bit for bit with served ones."""
     from paper_2104_10073_gb300 import zmc
 
-    ctx = zmc.Context(arena_bytes=2 << 30, quads_per_lane=zmc.SERVING_QUADS_PER_LANE)
+    ctx = zmc.Context(arena_bytes=2 << 30, quints_per_lane=zmc.SERVING_QUINTS_PER_LANE)
     yield ctx
     ctx.close()
 

@@ -24,7 +24,7 @@ int main(int argc, char **argv) {
   zmc_ctx k;
   k.gpu_name = "GPU X";
   k.sms = 10;
-  k.quads_per_lane = 16;
+  k.quints_per_lane = 16;
   k.kernel_regs[2] = 115;
   std::printf("key: %s\n", zmc::tune_key(&k, 2, 5).c_str());
   return 0;

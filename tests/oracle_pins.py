@@ -7,9 +7,9 @@ oracle disagrees with:
 * ``philox_vs_independent`` -- PyTorch's header-only Philox4x32-10 engine on
   random and boundary 128-bit counters and 64-bit keys (bit-exact);
 * ``word_layout`` -- the same independent engine at the counter each sample
-  coordinate is defined to use (word w = s*d + i, block w div 4, lane w mod 4,
-  counter (stream_id, block lo, block hi, 0), key = seed), including blocks past
-  2^32;
+  coordinate is defined to use (field c = s*d + i, block c div 5, bits
+  23 (c mod 5) .. +22 of the block's 128 bits, word 0 least significant; counter
+  (stream_id, block lo, block hi, 0), key = seed), including blocks past 2^32;
 * ``bruteforce_small`` -- an exact rational / 40-digit recomputation of the
   estimate and standard error from those independent words for N <= 16;
 * ``closed_forms`` -- the analytic integral of every family (paper, Fig. 1
@@ -68,6 +68,19 @@ def engine_triple(seed, stream_id, block):
     return (seed, block >> 32, stream_id | ((block & 0xFFFFFFFF) << 32))
 
 
+def engine_fields(indep, seed, stream_id, fields):
+    """The 23-bit fields ``fields`` (field indices of one stream) from the
+    independent engine: each block's four words joined into one Python integer
+    (word 0 least significant), field k of it = bits 23k .. 23k + 22."""
+    fields = [int(c) for c in fields]
+    words = indep([engine_triple(seed, stream_id, c // 5) for c in fields])
+    out = []
+    for c, w in zip(fields, words):
+        block = sum(int(w[j]) << (32 * j) for j in range(4))
+        out.append((block >> (23 * (c % 5))) & 0x7FFFFF)
+    return np.array(out, dtype=np.uint32)
+
+
 def _layout_rows():
     rows = []
     for d, sid, seed in [(1, 0, 0), (2, 7, 1), (3, 12345, 2**40 + 3), (4, 99, 5),
@@ -84,17 +97,12 @@ def word_layout(orc, indep):
         seed = int(row["seed"])
         sid = int(row["stream_id"])
         # a window at the start and one whose blocks straddle 2^32
-        for s0 in (0, (4 * 2**32) // d - 3):
+        for s0 in (0, (5 * 2**32) // d - 3):
             count = 6
-            words, _, _ = orc.samples(row, s0, count)
-            triples, lanes = [], []
-            for t in range(count):
-                for i in range(d):
-                    w = (s0 + t) * d + i
-                    triples.append(engine_triple(seed, sid, w >> 2))
-                    lanes.append(w & 3)
-            want = indep(triples)[np.arange(len(lanes)), lanes].reshape(count, d)
-            assert np.array_equal(words, want), (d, s0, words, want)
+            got, _, _ = orc.samples(row, s0, count)
+            want = engine_fields(indep, seed, sid,
+                                 [(s0 + t) * d + i for t in range(count) for i in range(d)])
+            assert np.array_equal(got, want.reshape(count, d)), (d, s0, got, want)
 
 
 # ------------------------------------------------------------------ brute force
@@ -142,11 +150,8 @@ def bruteforce_small(orc, indep, sizes=(1, 2, 3, 5, 16)):
         for v in wd:
             vol *= v
         nmax = max(sizes)
-        triples = [engine_triple(int(row["seed"]), int(row["stream_id"]), (s * d + i) >> 2)
-                   for s in range(nmax) for i in range(d)]
-        words = indep(triples)
-        lanes = [(s * d + i) & 3 for s in range(nmax) for i in range(d)]
-        r = words[np.arange(len(lanes)), lanes].reshape(nmax, d)
+        r = engine_fields(indep, int(row["seed"]), int(row["stream_id"]),
+                          range(nmax * d)).reshape(nmax, d)
         fs = []
         for s in range(nmax):
             xs = [lo[i] + wd[i] * mpmath.mpf(int(r[s, i]) & 0x7FFFFF) / 2**23

@@ -49,7 +49,7 @@ def test_struct_sizes(lib):
 
 def test_default_options(lib):
     o = zmc.zmc_default_options()
-    assert o.mem_budget_bytes == 1 << 30 and o.quads_per_lane == 0 and o.device == 0
+    assert o.mem_budget_bytes == 1 << 30 and o.quints_per_lane == 0 and o.device == 0
 
 
 def _bad(mutator):

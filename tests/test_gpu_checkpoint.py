@@ -17,7 +17,7 @@ from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
 
-CHUNK = 128 * zmc.SERVING_QUADS_PER_LANE  # samples per chunk of a serving context
+CHUNK = 160 * zmc.SERVING_QUINTS_PER_LANE  # samples per chunk of a serving context
 
 
 @pytest.fixture(scope="module")
@@ -146,7 +146,7 @@ def test_resume_from_moments_matches_oracle(sctx, sq_ctx):
     rng = np.random.default_rng(11)
     t = W.random_table(40, rng, n_lo=4, n_hi=300000, seed=4)
     n_all = t["n_samples"].astype(np.int64)
-    n0 = rng.integers(0, n_all + 1) // 4 * 4
+    n0 = rng.integers(0, n_all + 1) // 5 * 5
     n0[::7] = n_all[::7]  # some rows are complete already (any n_samples)
     n0[1::9] = 0          # some start afresh
     from_m = np.zeros(len(t), dtype=zmc.MOMENTS_DTYPE)
@@ -178,11 +178,11 @@ def test_resume_rejects_bad_moments(sctx):
     with pytest.raises(zmc.ZmcError) as e:
         zmc.zmc_submit_resume(sctx.handle, t, m)
     assert e.value.status == zmc.ZMC_EINVAL
-    m["n"] = [6, 0]  # not a multiple of 4
+    m["n"] = [6, 0]  # not a multiple of 5
     with pytest.raises(zmc.ZmcError) as e:
         zmc.zmc_submit_resume(sctx.handle, t, m)
     assert e.value.status == zmc.ZMC_EINVAL
-    m["n"] = [8, 0]
+    m["n"] = [10, 0]
     m["m2"] = [-1.0, 0.0]
     with pytest.raises(zmc.ZmcError) as e:
         zmc.zmc_submit_resume(sctx.handle, t, m)
@@ -212,7 +212,7 @@ def test_resume_combines_the_given_moments(sctx, sq_ctx):
     rng = np.random.default_rng(5)
     t = W.random_table(12, rng, n_lo=20000, n_hi=200000, seed=8)
     n_all = t["n_samples"].astype(np.int64)
-    na = n_all // 3 // 4 * 4
+    na = n_all // 3 // 5 * 5
     prior = np.zeros(len(t), dtype=zmc.MOMENTS_DTYPE)
     prior["n"] = na
     prior["mean"] = rng.uniform(-3.0, 3.0, len(t))

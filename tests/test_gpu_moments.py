@@ -17,7 +17,7 @@ from paper_2104_10073_gb300 import zmc
 from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
-CHUNK = 128 * zmc.DEFAULT_QUADS_PER_LANE  # samples per chunk at the default
+CHUNK = 160 * zmc.DEFAULT_QUINTS_PER_LANE  # samples per chunk at the default
 
 
 def _volumes(t):
@@ -57,7 +57,7 @@ def test_unaligned_pieces_match_oracle_moments(zctx):
     rows, b, e = [], [], []
     for i, r in enumerate(t):
         n = int(r["n_samples"])
-        a = int(rng.integers(0, n // 4)) * 4
+        a = int(rng.integers(0, n // 5)) * 5
         z = int(rng.integers(a + 1, n + 1))
         rows.append(i), b.append(a), e.append(z)
     m = zmc.zmc_integrate_moments(zctx.handle, t[rows], b, e)
@@ -81,8 +81,8 @@ def test_ranges_across_the_block_index_carry(zctx):
         for d in (1, 3, 4, 7):
             t = W.random_table(1, rng, n_lo=2**36, n_hi=2**36, families=[fam], dims=[d],
                                seed=fam * 10 + d)
-            s_carry = -(-(2**32) // d) * 4  # first sample whose blocks start past 2^32
-            a = (s_carry - 3 * CHUNK - 4 * d) // 4 * 4
+            s_carry = -(-(2**32) // d) * 5  # first sample whose blocks start past 2^32
+            a = (s_carry - 3 * CHUNK - 5 * d) // 5 * 5
             rows.append(t[0]), b.append(a), e.append(a + 7 * CHUNK + 13)
     tab = W.empty(len(rows))
     for i, r in enumerate(rows):
@@ -134,7 +134,8 @@ def test_sample_partition_over_ranks_on_device(zctx):
 
 def test_bad_ranges_are_rejected(zctx):
     t = W.harmonic_fig1(1000)[:2]
-    for b, e in (([2, 0], [10, 10]), ([0, 8], [10, 8]), ([0, 12], [10, 4])):
+    for b, e in (([2, 0], [10, 10]), ([8, 0], [10, 10]), ([0, 10], [10, 10]),
+                 ([0, 15], [10, 5])):
         with pytest.raises(zmc.ZmcError) as err:
             zmc.zmc_integrate_moments(zctx.handle, t, b, e)
         assert err.value.status == zmc.ZMC_EINVAL

@@ -1,7 +1,7 @@
 """CUDA path (through the C ABI) against the FP64 oracle on identical samples.
 
 Tolerances are stated in tests/gpu_common.py.  Sizes span many chunks and
-ragged tails (chunk = 128 * quads_per_lane = 8192 samples by default); the
+ragged tails (chunk = 128 * quints_per_lane = 8192 samples by default); the
 full-size mixed table runs in the benchmark's launch configuration and is
 checked on sampled rows the oracle computes one by one.
 """
@@ -112,7 +112,7 @@ def test_eval_samples_across_block_index_carry(zctx):
     for d in (1, 3, 7):
         t = W.empty(1)
         W.abslin(t[0], 1.0, [1.0] * d, [0.0] * d, [1.0] * d, 2**36, seed=9, stream_id=4)
-        s0 = (4 * 2**32) // d - 40
+        s0 = (5 * 2**32) // d - 40
         got = zmc.zmc_eval_samples(zctx.handle, t[0], s0, 80).astype(np.float64)
         _, _, want = oracle.samples(t[0], s0, 80)
         assert np.max(np.abs(got - want)) <= 4e-6 * G.sample_scale(t[0])
@@ -288,7 +288,7 @@ def test_chunk_length_changes_only_rounding():
     tab = W.random_table(30, np.random.default_rng(4), n_lo=100, n_hi=40000)
     want, _ = oracle.integrate(tab)
     for q in (1, 4, 64, 256):
-        with zmc.Context(arena_bytes=256 << 20, quads_per_lane=q) as c:
+        with zmc.Context(arena_bytes=256 << 20, quints_per_lane=q) as c:
             got = zmc.zmc_integrate(c.handle, tab)
         G.compare(tab, got, want)
 
@@ -306,7 +306,7 @@ def test_peaked_integrands_long_chunks():
                 int(rng.integers(3000, 60000)), seed=i, stream_id=i)
     want, _ = oracle.integrate(tab)
     for q in (16, 64, 256):
-        with zmc.Context(arena_bytes=256 << 20, quads_per_lane=q) as c:
+        with zmc.Context(arena_bytes=256 << 20, quints_per_lane=q) as c:
             got = zmc.zmc_integrate(c.handle, tab)
         G.compare(tab, got, want)
 

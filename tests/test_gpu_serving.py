@@ -110,7 +110,7 @@ def test_job_larger_than_budget_is_refused():
 def test_admission_waits_for_memory():
     """Jobs that do not all fit at once are admitted as earlier ones finish."""
     with zmc.Context(arena_bytes=12 << 20, serving=True, max_chunks_per_iter=4096) as c:
-        chunk = 128 * zmc.SERVING_QUADS_PER_LANE
+        chunk = 160 * zmc.SERVING_QUINTS_PER_LANE
         n = 2**31 // chunk * chunk  # 2^31 samples: 4 MiB of chunk records per job
         jobs = []
         for j in range(12):

@@ -41,7 +41,12 @@ MUTANTS = {
     "counter_words_swapped": (
         "uint32_t ctr[4] = {f->stream_id, (uint32_t)b, (uint32_t)(b >> 32), 0u};",
         "uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), f->stream_id, 0u};"),
-    "word_index": ("zo_word(f, s * (uint64_t)f->dim + i, cache)", "zo_word(f, s + i, cache)"),
+    "word_index": ("zo_field(f, s * (uint64_t)f->dim + i, cache)", "zo_field(f, s + i, cache)"),
+    "fields_per_block_4": ("uint64_t b = c / 5;", "uint64_t b = c / 4;"),
+    "field_stride_24": ("uint32_t first = 23u * (uint32_t)(c % 5);",
+                        "uint32_t first = 24u * (uint32_t)(c % 5);"),
+    "field_bit_order": ("r |= ((cache->words[q / 32] >> (q % 32)) & 1u) << j;",
+                        "r |= ((cache->words[q / 32] >> (31 - q % 32)) & 1u) << j;"),
     "map_width": ("x[i] = f->lo[i] + (f->hi[i] - f->lo[i]) * zo_uniform(r);",
                   "x[i] = f->lo[i] + f->hi[i] * zo_uniform(r);"),
     "volume_missing": ("estimate[j] = v * mean;", "estimate[j] = mean;"),
