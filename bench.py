@@ -696,9 +696,9 @@ def main():
     ap.add_argument("--skip-modes", action="store_true",
                     help="skip the functional, checkpoint/resume, user-integrand and "
                          "stratified (normal-mode) legs")
-    ap.add_argument("--cpu-repeats", type=int, default=40)
+    ap.add_argument("--cpu-repeats", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--quints-per-lane", type=int, default=64,
+    ap.add_argument("--quints-per-lane", type=int, default=104,
                     help="chunk length = 160 x this many samples")
     ap.add_argument("--serving-sweep", action="store_true")
     ap.add_argument("--serving-rates", type=float, nargs="+",

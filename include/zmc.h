@@ -123,7 +123,7 @@ typedef struct zmc_options {
                                     cache); never changes results                   */
     int32_t device;              /* CUDA device ordinal                              */
     uint32_t quints_per_lane;    /* chunk = 160 * quints_per_lane samples (a quint
-                                    is 5 consecutive samples); 0 -> 52, or 26 when
+                                    is 5 consecutive samples); 0 -> 104, or 26 when
                                     serving is set.
                                     Results are bit-identical for a fixed value and
                                     agree within rounding across values.            */
@@ -448,14 +448,14 @@ zmc_status zmc_normal_integrate_udf(zmc_ctx *ctx, const zmc_udf *udf, const doub
  * ZMC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.
  *   - At most ZMC_NOALLOC_MAX_FNS integrands (ZMC_EINVAL beyond) and at most
- *     ~1.6e10 samples in total at 8320 samples per chunk (ZMC_ENOMEM beyond, with
+ *     ~3.4e10 samples in total at 16640 samples per chunk (ZMC_ENOMEM beyond, with
  *     the needed size in zmc_last_error()).
  *   - All calls share the array and it keeps the previous call's contents; each
  *     call re-uploads its tables and zeroes its work counters.  Calls whose GPU
  *     work overlaps (other streams, or unordered host threads) race: order them.
  *   - The first call on a device looks up the array's device address with that
  *     device current; make it before any stream capture.
- *   - Results equal zmc_integrate's with the default quints_per_lane (52).      */
+ *   - Results equal zmc_integrate's with the default quints_per_lane (104).     */
 #define ZMC_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define ZMC_NOALLOC_MAX_FNS 4096u
 zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_result *out,

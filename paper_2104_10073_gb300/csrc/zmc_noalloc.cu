@@ -35,7 +35,7 @@ namespace {
 
 constexpr size_t kScratchBytes = ZMC_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kMaxFns = ZMC_NOALLOC_MAX_FNS;
-constexpr uint32_t kQuints = 52;  // the default chunk, so results equal zmc_integrate's
+constexpr uint32_t kQuints = 104;  // the default chunk, so results equal zmc_integrate's
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

@@ -853,7 +853,7 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   // longer chunks amortise the per-chunk work (keys, descriptor loads, warp
   // merge: 8192 samples measured fastest for whole tables); serving keeps them
   // at 4096, which measured lower job latency under load
-  if (opt.quints_per_lane == 0) opt.quints_per_lane = opt.serving ? 26 : 52;
+  if (opt.quints_per_lane == 0) opt.quints_per_lane = opt.serving ? 26 : 104;
   if (opt.quints_per_lane > 1024) return set_error(ZMC_EINVAL, "quints_per_lane above 1024");
   if (opt.arena && (reinterpret_cast<uintptr_t>(opt.arena) & 255))
     return set_error(ZMC_EINVAL, "arena must be 256-byte aligned");

@@ -292,16 +292,27 @@ zmc_status udf_run(zmc_ctx *ctx, const zmc_udf *udf, const UdfRow *rows, size_t 
   auto *ps = reinterpret_cast<double *>(s + o_p);
   for (size_t q = 0; q < params.size(); ++q)
     std::memcpy(ps + q * ZMC_NPARAM, params[q], ZMC_NPARAM * sizeof(double));
-  uint64_t item = 0;
   for (size_t i = 0; i < n; ++i) {
     fns[i] = tab[i];
     if (f64) set_param_address(&fns[i], d_p + static_cast<size_t>(prow[i]) * ZMC_NPARAM);
     fns[i].rec = d_rec + rec_off[i];
     fns[i].out = d_out + i;
-    ents[i].item_begin = item;
-    ents[i].fn = d_fns + i;
-    ents[i].chunk_begin = 0;
     mrg[i] = d_fns + i;
+  }
+  // the work list runs the rows grouped by variant (dimension and user function),
+  // so that consecutive work items, which co-resident warps take, use the same
+  // specialised code; records and results stay in row order, so the order
+  // changes no result
+  std::vector<uint32_t> order(n);
+  for (size_t i = 0; i < n; ++i) order[i] = static_cast<uint32_t>(i);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t a, uint32_t b) { return tab[a].variant < tab[b].variant; });
+  uint64_t item = 0;
+  for (size_t k = 0; k < n; ++k) {
+    const uint32_t i = order[k];
+    ents[k].item_begin = item;
+    ents[k].fn = d_fns + i;
+    ents[k].chunk_begin = 0;
     item += (rows[i].n_samples + chunk - 1) / chunk;
   }
   std::memset(hdr, 0, sizeof *hdr);

@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_EAGAIN",
                 8: "ZMC_ENOSYS"}
 ZMC_STAGE_SAMPLE, ZMC_STAGE_MERGE, ZMC_STAGE_ALL = 1, 2, 3
 ZMC_USER = 4
-DEFAULT_QUINTS_PER_LANE = 52  # the library's default chunk: 160 x 52 = 8320 samples
+DEFAULT_QUINTS_PER_LANE = 104  # the library's default chunk: 160 x 104 = 16640 samples
 SERVING_QUINTS_PER_LANE = 26  # ... and for a serving context: 4160 samples
 ZMC_UDF_F32, ZMC_UDF_F64 = 0, 1
 
