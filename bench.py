@@ -194,6 +194,21 @@ def oracle_rate(rows, threads=0):
     return W.total_samples(rows) / dt, used, dt
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (else the machine type)."""
+    import platform
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def fig1_table(rank: int):
     # weak scaling: rank r evaluates its own 10 repeats (keys 10r .. 10r+9)
     return W.harmonic_fig1(10**6, seeds=range(10 * rank, 10 * rank + 10))
@@ -221,7 +236,8 @@ def run_reference(args, world, rank):
         "config": {"workload": WORKLOAD, "sample": "100 integrands x 1e5 samples per step",
                    "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
-                         "sample": "Fig. 1 harmonics, key 0, 100 x 1e5 samples per step"},
+                         "sample": "Fig. 1 harmonics, key 0, 100 x 1e5 samples per step",
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -266,9 +282,15 @@ def run_native(args, world, rank, local):
     if rank == 0 and world == 1 and not args.skip_cpu:
         sample = W.harmonic_fig1(10**6, seeds=range(args.cpu_repeats))
         rate, used, dt = oracle_rate(sample)
+        one = W.harmonic_fig1(10**5, seeds=[0])
+        rate1, _, dt1 = oracle_rate(one, threads=1)
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
                "sample": f"Fig. 1 harmonics, keys 0..{args.cpu_repeats - 1}, "
-                         f"{len(sample)} x 1e6 samples ({dt:.1f} s wall)"}
+                         f"{len(sample)} x 1e6 samples ({dt:.1f} s wall)",
+               "cpu_model": cpu_model(),
+               "one_core": {"value": rate1 / 1e9, "unit": UNIT,
+                            "sample": f"Fig. 1 harmonics, key 0, 100 x 1e5 samples "
+                                      f"({dt1:.1f} s wall)"}}
 
     import tempfile
 
