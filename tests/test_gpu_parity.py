@@ -1,7 +1,7 @@
 """CUDA path (through the C ABI) against the FP64 oracle on identical samples.
 
 Tolerances are stated in tests/gpu_common.py.  Sizes span many chunks and
-ragged tails (chunk = 128 * quints_per_lane = 8192 samples by default); the
+ragged tails (chunk = 160 * quints_per_lane = 16640 samples by default); the
 full-size mixed table runs in the benchmark's launch configuration and is
 checked on sampled rows the oracle computes one by one.
 """
@@ -18,8 +18,10 @@ from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
 
-EDGE_SIZES = [1, 2, 3, 4, 5, 7, 8, 127, 128, 129, 2047, 2048, 2049, 4095, 4096, 4097, 8191,
-              8192, 8193, 10003, 16385, 65537]
+# around lane quints (5 samples), warp rounds (160), accumulation blocks (65 per
+# lane, 2080 per warp) and chunks (16640 by default, 4160 in serving contexts)
+EDGE_SIZES = [1, 2, 3, 4, 5, 6, 7, 9, 10, 11, 159, 160, 161, 2079, 2080, 2081, 4159, 4160,
+              4161, 8192, 10003, 16639, 16640, 16641, 33281, 65537]
 
 
 # ------------------------------------------------------------------ generator
