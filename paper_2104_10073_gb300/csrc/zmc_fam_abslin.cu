@@ -6,25 +6,41 @@
 namespace zmc {
 namespace {
 
-// a |c.x| (Eq. 2), as a |C + sum g_i v_i|: the g_i are FP32 roundings of FP64
-// constants; C carries the FP64 C plus the mean over the box of the dropped
-// low parts (sum (g_i - fl(g_i)) * 3/2), which removes their systematic effect.
+// a |c.x| (Eq. 2).  Near the hyperplane c.x = 0 the terms of c.x cancel, and a
+// sum rounded in FP32 keeps only an absolute accuracy of ~2^-24 of the terms;
+// so c.x is summed exactly instead, in units of 2^-F: the integer parts G_i m_i
+// (32 x 32 -> 64-bit products) in a 64-bit accumulator, whose modulo-2^64 wrap
+// is harmless because the true sum fits, and the sub-unit remainders g_i m_i in
+// FP32 (error a few units).  One rounding to FP32 at the end keeps the relative
+// accuracy of f down to |c.x| of a few 2^-F.
 template <int D, int G>
 struct Eval<ZMC_ABSLIN, D, G> {
-  float g[D];
-  float ch, cl, a;
+  int32_t gi[D];
+  float gl[D];
+  uint64_t g0;
+  float l0, scale;
   __device__ __forceinline__ void load(const FnDev *fn) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) g[i] = __uint_as_float(fn->w[i]);
-    ch = __uint_as_float(fn->w[14]);
-    cl = __uint_as_float(fn->w[15]);
-    a = __uint_as_float(fn->w[16]);
+    for (int i = 0; i < D; ++i) {
+      gi[i] = static_cast<int32_t>(fn->w[i]);
+      gl[i] = __uint_as_float(fn->w[7 + i]);
+    }
+    g0 = (static_cast<uint64_t>(fn->w[15]) << 32) | fn->w[14];
+    l0 = __uint_as_float(fn->w[16]);
+    scale = __uint_as_float(fn->w[17]);
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
-    float sh = ch;
+    uint64_t acc = g0;
+    float l = l0;
 #pragma unroll
-    for (int i = 0; i < D; ++i) sh = fmaf(g[i], unit_v(r[i]), sh);
-    return a * fabsf(sh + cl);
+    for (int i = 0; i < D; ++i) {
+      const uint32_t vb = (r[i] & 0x7FFFFFu) | 0x4B000000u;  // bits of 2^23 + m_i
+      acc += static_cast<uint64_t>(static_cast<int64_t>(gi[i]) *
+                                   static_cast<int64_t>(static_cast<int32_t>(vb)));
+      l = fmaf(gl[i], __uint_as_float(vb), l);
+    }
+    const float s = __ll2float_rn(static_cast<long long>(acc)) + l;
+    return scale * fabsf(s);
   }
 };
 

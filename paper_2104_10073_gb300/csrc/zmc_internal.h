@@ -56,9 +56,11 @@ __host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t di
 //             fl32(low word / 2^32) at w[7+i], fl32(2^23 - w[7+i] 2^23) at w[14+i];
 //             P0 (u32, units of 2^-32 turn, minus the folded 2^23 offsets) w[21];
 //             S R at w[22].
-//   ABSLIN    s = C + sum_i g_i v_i:  g_i = fl32(c_i (hi_i - lo_i)) at w[i];
-//             C = sum_i c_i (lo_i - (hi_i - lo_i)) + 3/2 sum_i (g_i - fl32(g_i)):
-//             hi w[14], lo w[15];  S a w[16].
+//   ABSLIN    s = c.x in units of 2^-F (F per integrand, host-chosen):
+//             s 2^F = G0 + sum_i G_i vb_i + L, vb_i = 0x4B000000 + m_i, exact in
+//             64-bit integers (modulo 2^64) plus L = l0 + sum_i g_i fl(2^23 + m_i)
+//             in FP32: G_i (s32) at w[i], g_i (FP32, |g_i| <= 1/2) at w[7+i],
+//             G0 (u64) at w[14] (lo), w[15] (hi), l0 at w[16], S a 2^-F at w[17].
 //   GAUSS     t_i = (x_i - mu_i) beta, beta = sqrt(log2(e) / 2) / sigma, so that
 //             f = A 2^(-sum t_i^2);  h_i = (hi_i - lo_i) beta: hi w[i], lo w[7+i];
 //             S A w[28].  Variant degree 0 ("near": mu_i / box position within

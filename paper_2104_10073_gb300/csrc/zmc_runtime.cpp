@@ -290,19 +290,48 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
       break;
     }
     case ZMC_ABSLIN: {
-      // s = C + sum g_i v_i (v_i in [1, 2)); the kernel uses fl32(g_i), so the
-      // mean 3/2 sum (g_i - fl32(g_i)) of the dropped parts goes into C
-      double C = 0.0;
+      // s = c.x = S0 + sum_i T_i m_i, S0 = c.lo, T_i = c_i w_i 2^-23, in units of
+      // 2^-F: G_i = round(T_i 2^F) fits 32 bits and |s| 2^F fits 63, so the kernel
+      // sums G_i m_i exactly in 64-bit integers (modulo 2^64; the true value fits)
+      // and the remainders g_i = T_i 2^F - G_i (|g_i| <= 1/2) in FP32.  It multiplies
+      // G_i by vb_i = 0x4B000000 + m_i, whose bits are also the float 2^23 + m_i,
+      // so the offsets G_i 0x4B000000 and 2^23 g_i are taken out of the constants.
+      double s0 = 0.0, tmax = 0.0, smax = 0.0;
       for (int i = 0; i < dim; ++i) {
-        const double g = p[1 + i] * w[i];
-        ok = ok && finite_f32(g);
-        const float gf = static_cast<float>(g);
-        std::memcpy(&fn->w[i], &gf, 4);
-        C += p[1 + i] * (d.lo[i] - w[i]) + 1.5 * (g - static_cast<double>(gf));
+        s0 += p[1 + i] * d.lo[i];
+        tmax = std::max(tmax, std::fabs(p[1 + i] * w[i]) * 0x1p-23);
+        smax += std::fabs(p[1 + i]) * std::max(std::fabs(d.lo[i]), std::fabs(d.hi[i]));
       }
-      ok = ok && finite_f32(C) && finite_f32(S * p[0]);
-      split(C, &fn->w[14], &fn->w[15]);
-      put_f32(&fn->w[16], S * p[0]);
+      if (!std::isfinite(s0) || !std::isfinite(smax) || !std::isfinite(tmax))
+        return set_error(ZMC_EINVAL, "abs-linear constants not finite");
+      int F = 1000;
+      if (tmax > 0.0) F = std::min(F, static_cast<int>(std::floor(std::log2(2147483647.0 / tmax))));
+      if (smax > 0.0) F = std::min(F, 61 - static_cast<int>(std::ceil(std::log2(smax))));
+      if (F == 1000) F = 0;
+      F = std::max(-900, F);
+      // log2 rounding can overshoot by one at a power of two: step down until
+      // every G_i fits 32 bits
+      for (int i = 0; i < dim; ++i)
+        while (std::fabs(std::ldexp(p[1 + i] * w[i] * 0x1p-23, F)) > 2147483647.0) --F;
+      uint64_t g0 = static_cast<uint64_t>(std::llround(std::ldexp(s0, F)));
+      float l0 = 0.0f;
+      double l0d = 0.0;
+      for (int i = 0; i < dim; ++i) {
+        const double t = std::ldexp(p[1 + i] * w[i] * 0x1p-23, F);
+        const int64_t G = std::llround(t);
+        const float gl = static_cast<float>(t - static_cast<double>(G));
+        fn->w[i] = static_cast<uint32_t>(static_cast<int32_t>(G));
+        std::memcpy(&fn->w[7 + i], &gl, 4);
+        g0 -= static_cast<uint64_t>(G) * 0x4B000000ull;
+        l0d -= static_cast<double>(gl) * 8388608.0;
+      }
+      l0 = static_cast<float>(l0d);
+      fn->w[14] = static_cast<uint32_t>(g0);
+      fn->w[15] = static_cast<uint32_t>(g0 >> 32);
+      std::memcpy(&fn->w[16], &l0, 4);
+      const double sc = S * p[0] * std::ldexp(1.0, -F);
+      ok = finite_f32(sc) && (sc == 0.0 || std::fabs(sc) >= 0x1p-126);
+      put_f32(&fn->w[17], sc);
       break;
     }
     case ZMC_GAUSS: {
