@@ -138,6 +138,20 @@ def test_integrate_edge_sizes_every_dim(zctx, fam):
     G.compare(tab, got, want)
 
 
+@pytest.mark.parametrize("fam", [W.HARMONIC, W.ABSLIN, W.GAUSS, W.POLY])
+def test_single_sample_rows_keep_relative_accuracy(zctx, fam):
+    """1500 rows of one sample each: the tolerance is then per sample and
+    relative, so every family must keep its relative accuracy wherever samples
+    fall, next to zeros of cos, of c.x and of the polynomial factors included
+    (an FP32 sum of c.x, for one, failed 91 of these 1500 abs-linear rows)."""
+    rng = np.random.default_rng(300 + fam)
+    t = W.random_table(1500, rng, n_lo=1, n_hi=1, families=[fam], seed=fam + 11)
+    t["stream_id"] = np.arange(len(t))
+    got = zmc.zmc_integrate(zctx.handle, t)
+    want, _ = oracle.integrate(t)
+    G.compare(t, got, want)
+
+
 def test_integrate_every_poly_degree(zctx):
     rng = np.random.default_rng(5)
     tab = W.empty(7 * 5 * 3)
