@@ -88,6 +88,17 @@ def test_validation_family_specific(lib):
     assert zmc.zmc_validate(t)[0] == zmc.ZMC_OK
 
 
+def test_validation_accepts_abslin_at_any_scale(lib):
+    """The exact abs-linear sum picks its fixed-point scale per integrand; tiny,
+    huge and mixed coefficient magnitudes and zero coefficients are all valid."""
+    for c in ([1e-20, -2e-20], [3e15, -1e15, 2e15], [1e8, 1e-8], [0.0, 1.0, 0.0], [0.0, 0.0],
+              [1e-300, 1.0], [1e30, -1e30]):
+        t = W.empty(1)
+        W.abslin(t[0], 1.0, c, [-1.0] * len(c), [1.0] * len(c), 10)
+        st, bad, msg = zmc.zmc_validate(t)
+        assert st == zmc.ZMC_OK, (c, msg)
+
+
 def test_validation_of_an_empty_table(lib):
     st, bad, _ = zmc.zmc_validate(W.empty(0))
     assert st == zmc.ZMC_OK and bad is None

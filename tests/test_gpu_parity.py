@@ -152,6 +152,39 @@ def test_single_sample_rows_keep_relative_accuracy(zctx, fam):
     G.compare(t, got, want)
 
 
+def _abslin_scale_rows():
+    """Abs-linear rows whose fixed-point scale 2^-F lands far from the usual:
+    tiny, huge and mixed coefficient magnitudes, zero coefficients, boxes far
+    from the origin and hyperplanes through the box."""
+    rows = []
+    rng = np.random.default_rng(77)
+    cases = [([1e-20, -2e-20], [-1.0, 0.0], [1.0, 2.0]),
+             ([3e15, -1e15, 2e15], [-1.0, -1.0, 0.0], [0.5, 1.0, 2.0]),
+             ([1e8, 1e-8], [0.0, 0.0], [1.0, 1.0]),
+             ([0.0, 1.0, 0.0], [-1.0, -1.0, -1.0], [1.0, 1.0, 1.0]),
+             ([0.0, 0.0], [0.0, 0.0], [1.0, 1.0]),
+             ([1.0, -1.0], [1e3, 1e3], [1e3 + 1.0, 1e3 + 1.0]),
+             ([1.0] * 7, [-0.5] * 7, [0.5] * 7),
+             ([1.0, 1.0, -1.0], [-3e-9, -1e-9, -2e-9], [1e-9, 2e-9, 3e-9])]
+    for c, lo, hi in cases:
+        for n in (1, 7, 1000):
+            t = W.empty(1)
+            W.abslin(t[0], float(rng.uniform(0.5, 2.0)), c, lo, hi, n, seed=n,
+                     stream_id=len(rows))
+            rows.append(t[0])
+    tab = W.empty(len(rows))
+    for i, r in enumerate(rows):
+        tab[i] = r
+    return tab
+
+
+def test_abslin_fixed_point_scale_edge_cases(zctx):
+    t = _abslin_scale_rows()
+    got = zmc.zmc_integrate(zctx.handle, t)
+    want, _ = oracle.integrate(t)
+    G.compare(t, got, want)
+
+
 def test_integrate_every_poly_degree(zctx):
     rng = np.random.default_rng(5)
     tab = W.empty(7 * 5 * 3)
