@@ -51,6 +51,22 @@ def harmonic_ops_per_sample(d: int) -> float:
     return 8 * d + 0.8 * d + 4 * d + 5 + 6 + 3
 
 
+# Algorithmic work of a d-dimensional harmonic sample on the fmaheavy pipe (the
+# pipe that executes integer multiplies), in 32-bit multiply-add lane-operations:
+# a widening 32 x 32 -> 64 multiply counts 2 (it takes the pipe twice as long as
+# a 32-bit one).  Philox: 16 widening multiplies per block once the products
+# shared by a chunk are formed once, d / 5 blocks per sample -> 6.4 d; the
+# fixed-point phase: one 32-bit multiply-add per coordinate -> d.
+def harmonic_heavy_ops_per_sample(d: int) -> float:
+    return 2 * 16 * d / 5 + d
+
+
+def table_mean(table, fn) -> float:
+    """Sample-weighted mean of fn(dim) over a table's rows."""
+    n = table["n_samples"].astype(np.float64)
+    return float(np.sum(n * np.array([fn(int(d)) for d in table["dim"]])) / np.sum(n))
+
+
 # Sources of the dominant kernel (zmc_batched_kernel<HARMONIC>).
 KERNEL_SOURCES = ["paper_2104_10073_gb300/csrc/zmc_fam_harmonic.cu",
                   "paper_2104_10073_gb300/csrc/zmc_device.cuh",
@@ -83,6 +99,80 @@ def profile_counters():
     if prof.get("kernel_source_sha256") != kernel_source_hash():
         return None
     return prof
+
+
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml, by
+    ctypes; read-only queries) every ``period`` seconds on a thread while the
+    timed region runs: a ~50 ms region still gets dozens of samples."""
+
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap"}
+
+    def __init__(self, device: int, period: float = 0.001):
+        import ctypes
+
+        self.period = period
+        self.samples = []
+        self.stop_flag = threading.Event()
+        self.thread = None
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.nv = nv
+        self.h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+        except Exception:  # noqa: BLE001 - older torch: fall back to the index
+            uuid = None
+        rc = 1
+        if uuid:
+            rc = nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h))
+        if rc != 0:
+            rc = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device), ctypes.byref(self.h))
+        if rc != 0:
+            raise OSError("no NVML handle")
+        self.get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        self.max_mhz = None
+        if nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(v)) == 0:
+            self.max_mhz = float(v.value)
+
+    def _read(self):
+        import ctypes
+
+        mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if (self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz)) == 0 and
+                    self.get_reasons(self.h, ctypes.byref(rs)) == 0):
+                self.samples.append((float(mhz.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def start(self):
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag.set()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [m for m, _ in self.samples]
+        reasons = sorted({nm for _, r in self.samples for bit, nm in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(sm), "sm_mhz_min": min(sm) if sm else None,
+                "source": f"NVML every {1e3 * self.period:.0f} ms"}
+
+
+def clock_sampler(device: int):
+    """The NVML sampler where libnvidia-ml loads, else the nvidia-smi one."""
+    try:
+        return NvmlClockSampler(device)
+    except (OSError, AttributeError):
+        return ClockSampler(device)
 
 
 class ClockSampler:
@@ -139,7 +229,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi -lms 100"}
 
 
 def dist_setup():
@@ -295,7 +385,10 @@ def run_native(args, world, rank, local):
     import tempfile
 
     tune_path = os.path.join(tempfile.gettempdir(), f"zmc_tune_{os.getuid()}_{local}.json")
-    ctx = zmc.Context(arena_bytes=2 << 30, device=local, autotune=not args.no_autotune,
+    # the autotuner picks the launch geometry, the chunk length and the unroll
+    # (cached per GPU and table shape; --no-autotune: --quints-per-lane, unroll 1)
+    tune = 0 if args.no_autotune else zmc.ZMC_TUNE_GEOMETRY | zmc.ZMC_TUNE_CHUNK
+    ctx = zmc.Context(arena_bytes=2 << 30, device=local, autotune=tune,
                       tune_cache_path=tune_path, quints_per_lane=args.quints_per_lane)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     tab = fig1_table(rank)
@@ -306,7 +399,7 @@ def run_native(args, world, rank, local):
         zmc.zmc_plan_run(plan)
     ctx.stream.synchronize()
 
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -367,30 +460,14 @@ def run_native(args, world, rank, local):
         assert np.all(out["status"] == 0)
         e2e_s = max_over_ranks(world, sum(e2e_t) / len(e2e_t))
 
-    # the 10^4-integrand mix (batched and plain), rank 0 only
-    mixed = None
+    # the 10^4-integrand mix and the Eq. 2 abs-linear set (batched and plain),
+    # rank 0 only
+    mixed = eq2 = None
     if rank == 0 and not args.skip_mixed:
-        mt = W.mixed(10**4)
-        mp = zmc.zmc_plan_create(ctx.handle, mt)
-        zmc.zmc_plan_run(mp)
-        ctx.stream.synchronize()
-        st, _ = time_plan(zmc, torch, ctx, mp, 3, flush)
-        ns = W.total_samples(mt)
-        mixed = {"workload": "mixed-1e4-integrands-d1..7-logN4..7", "samples": ns,
-                 "batched_gsps": ns / (statistics.median(st) / 1e3) / 1e9,
-                 "batched_ms": statistics.median(st)}
-        if not args.skip_plain:
-            zmc.zmc_plan_run_plain(mp)
-            ctx.stream.synchronize()
-            e0.record(ctx.stream)
-            zmc.zmc_plan_run_plain(mp)
-            e1.record(ctx.stream)
-            ctx.stream.synchronize()
-            pms = e0.elapsed_time(e1)
-            mixed["plain_gsps"] = ns / (pms / 1e3) / 1e9
-            mixed["plain_ms"] = pms
-            mixed["batched_over_plain"] = mixed["batched_gsps"] / mixed["plain_gsps"]
-        zmc.zmc_plan_destroy(mp)
+        mixed = batched_and_plain(zmc, torch, ctx, W.mixed(10**4), flush,
+                                  "mixed-1e4-integrands-d1..7-logN4..7", 5, not args.skip_plain)
+        eq2 = batched_and_plain(zmc, torch, ctx, W.abslin_eq2(10**6), flush,
+                                "eq2-abslin-49x2d-51x3d-x1e6", 20, not args.skip_plain)
 
     # the generator alone: Philox4x32-10 blocks/s, the ceiling of any sampling
     # kernel (a 4-D sample draws 4/5 of a block); measured after the timed region
@@ -417,57 +494,134 @@ def run_native(args, world, rank, local):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the harmonic family's persistent launch)
+    # Roofline of the dominant kernel (the harmonic family's persistent launch).
+    # The binding resource is the busiest pipe in the committed ncu summary of
+    # this kernel source; achieved = the algorithmic work on that pipe per launch
+    # / the launch's CUDA-event time.  The issue-slot figure (every algorithmic
+    # operation against 1 instruction per scheduler per cycle) and the measured
+    # generator ceiling are given beside it.
     sm_clock = peaks.get("sm_max_mhz", 2070.0)
     sms = info["sms"]
-    peak_gops = sms * 128 * sm_clock * 1e6 / 1e9
-    ops = harmonic_ops_per_sample(4) * n_samples
-    achieved = ops / (kms / 1e3) / 1e9
+    sched_ghz = sms * 4 * sm_clock * 1e6 / 1e9  # schedulers x clock, G cycles/s
+    ops_ps = table_mean(tab, harmonic_ops_per_sample)
+    heavy_ps = table_mean(tab, harmonic_heavy_ops_per_sample)
+    issue_peak = sched_ghz * 32  # G lane-instructions/s
+    issue_ach = ops_ps * n_samples / (kms / 1e3) / 1e9
+    heavy_peak = sched_ghz * 16  # G 32-bit multiply-add lane-ops/s (16 lanes per scheduler)
+    heavy_ach = heavy_ps * n_samples / (kms / 1e3) / 1e9
     prof = profile_counters()
+    pipes = prof["pipes"] if prof else None
+    busiest = None
+    if pipes:
+        busiest = max((k for k in pipes if k != "issue_active"), key=lambda k: pipes[k])
+    roofline = {
+        "bound": busiest or "alu", "bound_class": "alu",
+        "achieved": heavy_ach, "peak": heavy_peak,
+        "unit": "G fmaheavy lane-ops/s (32-bit multiply-add = 1, widening = 2)",
+        "frac": heavy_ach / heavy_peak,
+        "traffic": prof["dram_bytes_per_launch"] if prof else None,
+        "kernel": "zmc_batched_kernel<HARMONIC>", "kernel_ms": kms,
+        "peak_basis": f"{sms} SMs x 4 schedulers x 16 lanes x {sm_clock:.0f} MHz (measured max)",
+        "heavy_ops_per_sample": heavy_ps,
+        "issue_slots": {"achieved": issue_ach, "peak": issue_peak, "unit": "G lane-op/s",
+                        "frac": issue_ach / issue_peak, "ops_per_sample": ops_ps},
+        "ncu_pipes": pipes,
+        "ncu_profile": os.path.relpath(PROFILE, ROOT) if prof else "stale (kernel source changed)",
+        "generator_ceiling_frac": generator["harmonic_over_ceiling"] if generator else None,
+    }
+    bop = None if plain_ms is None else plain_ms / (sum(step_ms) / len(step_ms))
+    summary = {
+        "batched_gsps": sig(value), "plain_fp64_gsps": sig(n_samples / (plain_ms / 1e3) / 1e9)
+        if plain_ms else None, "batched_over_plain": sig(bop),
+        "per_integrand_fp32_gsps": sig(n_samples / (per_row_ms / 1e3) / 1e9) if per_row_ms else None,
+        "batching_alone_x": sig(per_row_ms / (sum(step_ms) / len(step_ms))) if per_row_ms else None,
+        "e2e_gsps": sig(total / e2e_s / 1e9) if e2e_s else None,
+        "fmaheavy_frac": sig(roofline["frac"], 3),
+        "issue_frac": sig(roofline["issue_slots"]["frac"], 3),
+    }
+    for key, leg in (("mix1e4", mixed), ("eq2_abslin", eq2)):
+        if leg:
+            summary[key] = {"batched_gsps": sig(leg["batched_gsps"]),
+                            "plain_fp64_gsps": sig(leg.get("plain_gsps")),
+                            "batched_over_plain": sig(leg.get("batched_over_plain"))}
+    if serving:
+        summary["serving"] = {"jobs_per_s": serving["rate_jobs_per_s"],
+                              "p50_ms": sig(serving["p50_ms"], 3), "p99_ms": sig(serving["p99_ms"], 3),
+                              "gsps": sig(serving["samples_per_s"], 3)}
+    # Long per-mode records first; the contract keys and the metric summary last,
+    # so that a reader of the line's tail sees them.
     line = {
+        "functional": functional, "checkpoint": checkpoint, "udf": udf, "normal": normal,
+        "generator": generator,
+        "plain": None if plain_ms is None else {
+            "value": n_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": plain_ms,
+            "dtype": "f64", "form": "one FP64 kernel launch per integrand + merge"},
+        "per_integrand_fp32": None if per_row_ms is None else {
+            "value": n_samples / (per_row_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": per_row_ms,
+            "form": "the batched FP32 kernels, one launch (graph) per integrand"},
+        "mixed": mixed, "eq2_abslin": eq2, "serving": serving,
+        "wall_s_timed": wall,
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "integrands": len(tab), "samples_per_step": n_samples,
                    "quints_per_lane": info["quints_per_lane"], "chunks": info["n_chunks"],
+                   "unroll": info["family_unroll"][0],
                    "grid": info["family_grid"][0], "block": info["family_block"][0],
                    "autotune": ["default", "measured", "cached"][info["tune_source"][0]],
+                   "chunk_tune": ["default", "measured", "cached"][info["chunk_tune_source"]],
                    "l2": "flushed between steps (256 MiB write, outside the timed events)"},
-        "plain": None if plain_ms is None else {
-            "value": n_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": plain_ms,
-            "dtype": "f64", "form": "one FP64 kernel launch per integrand + merge"},
-        "batched_over_plain": None if plain_ms is None else plain_ms / (sum(step_ms) / len(step_ms)),
-        "per_integrand_fp32": None if per_row_ms is None else {
-            "value": n_samples / (per_row_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": per_row_ms,
-            "form": "the batched FP32 kernels, one launch (graph) per integrand",
-            "batched_over_this": per_row_ms / (sum(step_ms) / len(step_ms))},
-        "mixed": mixed,
-        "functional": functional,
-        "checkpoint": checkpoint,
-        "udf": udf,
-        "normal": normal,
-        "serving": serving,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
         "e2e": None if e2e_s is None else {
             "value": total / e2e_s / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": len(tab) * W.DESC_DTYPE.itemsize,
             "d2h_bytes_per_step": len(tab) * 32,
             "path": "zmc_integrate (host table in, host results out)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved / peak_gops,
-                     "traffic": prof["dram_bytes_per_launch"] if prof else None,
-                     "kernel": "zmc_batched_kernel<HARMONIC>",
-                     "kernel_ms": kms,
-                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz issue slots",
-                     "ops_per_sample": harmonic_ops_per_sample(4),
-                     "ncu_pipes": prof["pipes"] if prof else None},
-        "generator": generator,
-        "cpu_baseline": cpu,
-        "clocks": clk,
         "gpu_launches": 2 * args.steps,
-        "wall_s_timed": wall,
+        "clocks": clk,
+        "batched_over_plain": bop,
+        "summary": summary,
     }
     print(json.dumps(line), flush=True)
+
+
+def batched_and_plain(zmc, torch, ctx, table, flush, name, steps, plain):
+    """Batched rate (median of ``steps`` device-timed plan replays, L2 flushed
+    before each) and plain FP64 rate (one pass, one launch per integrand) of one
+    table."""
+    plan = zmc.zmc_plan_create(ctx.handle, table)
+    zmc.zmc_plan_run(plan)
+    ctx.stream.synchronize()
+    st, _ = time_plan(zmc, torch, ctx, plan, steps, flush)
+    ns = W.total_samples(table)
+    out = {"workload": name, "integrands": len(table), "samples": ns,
+           "batched_gsps": ns / (statistics.median(st) / 1e3) / 1e9,
+           "batched_ms": statistics.median(st)}
+    res = zmc.zmc_plan_results(plan, len(table))
+    assert np.all(res["status"] == 0)
+    if plain:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        zmc.zmc_plan_run_plain(plan)
+        ctx.stream.synchronize()
+        e0.record(ctx.stream)
+        zmc.zmc_plan_run_plain(plan)
+        e1.record(ctx.stream)
+        ctx.stream.synchronize()
+        pms = e0.elapsed_time(e1)
+        out["plain_gsps"] = ns / (pms / 1e3) / 1e9
+        out["plain_ms"] = pms
+        out["batched_over_plain"] = out["batched_gsps"] / out["plain_gsps"]
+    zmc.zmc_plan_destroy(plan)
+    return out
+
+
+def sig(x, digits=4):
+    """x rounded to ``digits`` significant digits (None stays None)."""
+    if x is None:
+        return None
+    return float(f"{x:.{digits}g}")
 
 
 def run_serving(zmc, device, rate_hz, seconds, quints_per_lane=0, chunks_per_iter=0):
@@ -721,7 +875,7 @@ def main():
     ap.add_argument("--cpu-repeats", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--quints-per-lane", type=int, default=104,
-                    help="chunk length = 160 x this many samples")
+                    help="chunk length = 160 x this many samples (with --no-autotune)")
     ap.add_argument("--serving-sweep", action="store_true")
     ap.add_argument("--serving-rates", type=float, nargs="+",
                     default=[10.0, 30.0, 100.0, 300.0, 1000.0])

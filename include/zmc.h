@@ -75,8 +75,20 @@ typedef enum zmc_status {
 } zmc_status;
 
 /* One integrand (464 bytes, naturally aligned, no padding beyond `deg`).
- * Valid: family in 0..3, 1 <= dim <= 7, n_samples >= 1, lo_i < hi_i finite,
- * deg <= 4 (ZMC_POLY; 0 otherwise), sigma > 0 (ZMC_GAUSS), finite parameters.
+ * Valid: family in 0..3, 1 <= dim <= 7, 1 <= n_samples <= 2^62, lo_i < hi_i
+ * finite, deg <= 4 (ZMC_POLY; 0 otherwise), sigma > 0 (ZMC_GAUSS), all 40
+ * parameters finite, and the FP32 evaluation constants derived from them in
+ * range:
+ *   - ZMC_HARMONIC: |k_i (hi_i - lo_i)| / (2 pi) <= 2^20 turns per dimension and
+ *     |k.lo - atan2(b, a)| / (2 pi) < 4e15 turns (the fixed-point phase), and
+ *     sqrt(a^2 + b^2) times the power-of-two scale finite in FP32;
+ *   - ZMC_ABSLIN: c.lo, sum |c_i| max(|lo_i|, |hi_i|) finite, and a 2^-F times
+ *     the scale a normal FP32 number or 0 (F the fixed-point exponent of c.x);
+ *   - ZMC_GAUSS, ZMC_POLY: every scaled constant (amplitude, 1/sigma terms,
+ *     coefficients re-expanded on the unit box) finite in FP32.
+ * (The scale is 2^(48 - ceil(log2 B)), B a bound of |f| on the box, clamped
+ * to 2^-100 .. 2^100.)  A row outside these rules is rejected with ZMC_EINVAL
+ * and a reason in zmc_last_error(); zmc_validate applies the same rules.
  * Entries of lo/hi/p beyond the family's use are ignored.                      */
 typedef struct zmc_desc {
     uint32_t family;
@@ -118,9 +130,21 @@ typedef struct zmc_options {
     void *stream;                /* cudaStream_t for all work; NULL -> the library
                                     creates a non-blocking stream                   */
     uint32_t max_chunks_per_iter;/* serving: chunks per persistent launch; 0 -> auto */
-    uint32_t autotune;           /* 1: time launch geometries of each family kernel
-                                    on a slice of a new plan's work (or reuse the
-                                    cache); never changes results                   */
+    uint32_t autotune;           /* flags (0: none):
+                                    ZMC_TUNE_GEOMETRY: time launch geometries of each
+                                    family kernel on a slice of a new plan's work (or
+                                    reuse the cache); never changes results.
+                                    ZMC_TUNE_CHUNK: also pick, per plan, the chunk
+                                    length (quints_per_lane among 26, 52, 104, 208)
+                                    and each family kernel's quint-loop unroll (1 or
+                                    2), timed on a bounded subset of the table's rows
+                                    and cached by the table's shape class (families,
+                                    dominant dimensions, size).  Both change results
+                                    within rounding only: results are bit-identical
+                                    for a given choice (zmc_plan_info reports it),
+                                    and unroll 1 is the untuned kernel.  Plans
+                                    of sample ranges (zmc_integrate_moments) keep
+                                    quints_per_lane.                                */
     int32_t device;              /* CUDA device ordinal                              */
     uint32_t quints_per_lane;    /* chunk = 160 * quints_per_lane samples (a quint
                                     is 5 consecutive samples); 0 -> 104, or 26 when
@@ -131,6 +155,9 @@ typedef struct zmc_options {
     uint32_t serving;            /* 1: start the serving thread (zmc_submit/poll)    */
     uint32_t reserved;
 } zmc_options;
+
+#define ZMC_TUNE_GEOMETRY 1u
+#define ZMC_TUNE_CHUNK 2u
 
 typedef struct zmc_ctx zmc_ctx;
 typedef struct zmc_plan zmc_plan;
@@ -147,6 +174,10 @@ typedef struct zmc_plan_info {
     uint32_t family_block[4];  /* polynomial); block 0 = family absent             */
     int32_t tune_source[4];    /* 0 default geometry, 1 measured by the autotuner,  */
                                /* 2 taken from the autotune cache                   */
+    uint32_t family_unroll[4]; /* quint-loop unroll of each family kernel (1 or 2)  */
+    int32_t chunk_tune_source; /* chunk length and unroll: 0 default (quints_per_lane
+                                  of the context, unroll 1), 1 measured, 2 cached   */
+    uint32_t reserved;
 } zmc_plan_info;
 
 typedef struct zmc_serving_stats {
@@ -154,6 +185,8 @@ typedef struct zmc_serving_stats {
     uint64_t iterations;         /* persistent launches so far                     */
     uint64_t samples_done;
     uint64_t arena_used_bytes, arena_bytes;
+    uint64_t shared_iterations;  /* launches whose work items came from >= 2 jobs   */
+    uint64_t max_jobs_per_iter;  /* most jobs with work items in one launch so far  */
 } zmc_serving_stats;
 
 /* Fill *opt with defaults (1 GiB arena, own stream, device 0, no autotune). */
@@ -445,16 +478,23 @@ zmc_status zmc_normal_integrate_udf(zmc_ctx *ctx, const zmc_udf *udf, const doub
  * the current device: read `out` after synchronising the stream.  It needs no
  * context and allocates nothing: its launch header, work list, device
  * descriptors and partial sums live in one fixed array of
- * ZMC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
- * loads the library holds until the process exits.
+ * ZMC_NOALLOC_SCRATCH_BYTES compiled into the library.  A device reserves the
+ * array once the library's device code is loaded there (with CUDA's lazy module
+ * loading, at the latest on the first call on that device) and holds it until
+ * the process exits.
  *   - At most ZMC_NOALLOC_MAX_FNS integrands (ZMC_EINVAL beyond) and at most
  *     ~3.4e10 samples in total at 16640 samples per chunk (ZMC_ENOMEM beyond, with
  *     the needed size in zmc_last_error()).
  *   - All calls share the array and it keeps the previous call's contents; each
  *     call re-uploads its tables and zeroes its work counters.  Calls whose GPU
  *     work overlaps (other streams, or unordered host threads) race: order them.
- *   - The first call on a device looks up the array's device address with that
- *     device current; make it before any stream capture.
+ *   - The tables are uploaded from a static host buffer.  Before a call
+ *     rewrites it, the call waits until the previous call's upload has run on
+ *     the GPU, so a call may block until the previous call's stream reaches
+ *     that upload.
+ *   - The first call on a device looks up the array's device address and
+ *     creates one event (no memory allocation) with that device current; make
+ *     it before any stream capture.
  *   - Results equal zmc_integrate's with the default quints_per_lane (104).     */
 #define ZMC_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define ZMC_NOALLOC_MAX_FNS 4096u

@@ -1,10 +1,10 @@
 """Build ``libzmc.so`` (the C ABI library) in-tree with nvcc for sm_103a.
 
-The translation units (one per integrand family's sampling path, the plain form,
-the shared kernels, the host runtime, serving, the allocation-free entry point,
-the tuning cache) compile in parallel and link into one shared library with the
-CUDA runtime linked statically, so the library needs only the NVIDIA driver at
-run time.  Output:
+The translation units (one per integrand family's sampling path and quint-loop
+unroll, the plain form, the shared kernels, the host runtime, serving, the
+allocation-free entry point, the tuning cache) compile in parallel and link into
+one shared library with the CUDA runtime linked statically, so the library needs
+only the NVIDIA driver at run time.  Output:
 ``paper_2104_10073_gb300/libzmc.so``.  Rebuilds only when a source is newer.
 """
 from __future__ import annotations
@@ -22,10 +22,12 @@ OUT = os.path.join(PKG, "libzmc.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["zmc_fam_harmonic.cu", "zmc_fam_abslin.cu", "zmc_fam_gauss.cu", "zmc_fam_poly.cu",
-           "zmc_plain.cu", "zmc_kernels.cu", "zmc_runtime.cpp", "zmc_serving.cpp",
-           "zmc_noalloc.cu", "zmc_tune.cpp", "zmc_udf.cpp", "zmc_normal.cpp", "zmc_pool.cpp",
-           "zmc_polyroots.cpp"]
+FAMILY_SOURCES = ["zmc_fam_harmonic.cu", "zmc_fam_abslin.cu", "zmc_fam_gauss.cu",
+                  "zmc_fam_poly.cu"]
+SOURCES = [*FAMILY_SOURCES, "zmc_plain.cu", "zmc_kernels.cu", "zmc_runtime.cpp",
+           "zmc_serving.cpp", "zmc_noalloc.cu", "zmc_tune.cpp", "zmc_udf.cpp", "zmc_normal.cpp",
+           "zmc_pool.cpp", "zmc_polyroots.cpp"]
+UNROLLS = (1, 2)  # each family file is compiled once per quint-loop unroll
 HEADERS = ["zmc_internal.h", "zmc_runtime.h", "zmc_coeffs.h", "zmc_device.cuh",
            "zmc_udf_kernel.cuh", "zmc_udf_layout.h"]
 # Headers whose text zmc_udf.cpp hands to NVRTC (symbol name, path).
@@ -34,6 +36,21 @@ JIT_HEADERS = [("kJitZmcH", os.path.join(INCLUDE, "zmc.h")),
                ("kJitZmcDeviceCuh", os.path.join(CSRC, "zmc_device.cuh")),
                ("kJitZmcUdfKernelCuh", os.path.join(CSRC, "zmc_udf_kernel.cuh")),
                ("kJitZmcUdfLayoutH", os.path.join(CSRC, "zmc_udf_layout.h"))]
+
+
+def _units():
+    """(source, object stem, extra flags) of every translation unit."""
+    units = []
+    for src in SOURCES:
+        stem = os.path.splitext(src)[0]
+        if src in FAMILY_SOURCES:
+            # -fmad=false: no multiply-add is fused unless the source says fmaf, so
+            # the sampling arithmetic is exactly as written whatever the unroll
+            units += [(src, f"{stem}_u{u}", [f"-DZMC_FAM_UNROLL={u}", "-fmad=false"])
+                      for u in UNROLLS]
+        else:
+            units.append((src, stem, []))
+    return units
 
 
 def _nvcc() -> str:
@@ -90,9 +107,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     _write_jit_sources()
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, stem, extra = unit
+        obj = os.path.join(BUILD, stem + ".o")
+        cmd = [nvcc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v" if verbose else "-Xptxas=-O3")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -102,8 +120,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    units = _units()
+    # the slowest unit (the polynomial family) first, so it overlaps the rest
+    units.sort(key=lambda u: u[0] != "zmc_fam_poly.cu")
+    with ThreadPoolExecutor(max_workers=len(units)) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = OUT + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-cudart", "static", *objs, "-o", tmp,
            "-lpthread", "-ldl"]

@@ -187,6 +187,14 @@ __device__ __forceinline__ void gen_quint_fast(uint32_t base_lo, const StreamPre
     block_fields(philox_block(base_lo + static_cast<uint32_t>(j), sp), r + 5 * j);
 }
 
+// Packed FP32 (sm_100 and later): one instruction issues the operation on both
+// halves of a pair, each half rounded exactly as the scalar operation would be.
+// The sampling loop is bound by issue slots, so pairs of independent FP32
+// operations are issued this way where their operands come in pairs.
+#ifndef ZMC_PACKED_F32
+#define ZMC_PACKED_F32 1
+#endif
+
 __device__ __forceinline__ float unit_v(uint32_t word) {
   // v = 1 + (word & 0x7FFFFF) * 2^-23 in [1, 2), exact: one LOP3.
   return __uint_as_float((word & 0x7FFFFFu) | 0x3F800000u);
@@ -196,11 +204,55 @@ __device__ __forceinline__ float unit_v(uint32_t word) {
 // Eval<FAM, D, G>: load(fn) reads the integrand's FP32 constants from FnDev;
 // operator()(r) returns the scaled value f' = S f at the sample whose D 23-bit
 // fields are the low 23 bits of r[0..D).  Specialised per family in
-// zmc_fam_<family>.cu.
+// zmc_fam_<family>.cu.  An Eval's last operation is a rounded one (an explicit
+// _rn product or an fmaf): a plain product could be contracted into an FMA with
+// the sums' f - K, differently in differently unrolled loops, which would make
+// the unroll change results.
 template <int FAM, int D, int G>
 struct Eval;
 
+// An Eval may also provide quint(r, f): the five values of a quint at once (its
+// fields r[0 .. 5D)), computed with packed FP32 pairs; equal to f[t] = (*this)(r
+// + t D) bit for bit.  eval_quint uses it when present.
+template <class T>
+struct VoidOf {
+  typedef void type;
+};
+template <class E, class = void>
+struct HasQuint {
+  static constexpr bool value = false;
+};
+template <class E>
+struct HasQuint<E, typename VoidOf<decltype(&E::quint)>::type> {
+  static constexpr bool value = true;
+};
+
+template <int D, class E>
+__device__ __forceinline__ void eval_quint(const E &ev, const uint32_t (&r)[5 * D],
+                                           float (&f)[5]) {
+  if constexpr (HasQuint<E>::value && ZMC_PACKED_F32) {
+    ev.quint(r, f);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 5; ++t) f[t] = ev(r + t * D);
+  }
+}
+
 // ---------------------------------------------------------------- one chunk
+// One step of Chan's pairwise merge: (n, mean, m2) absorbs (nb, mb, m2b), nb > 0.
+// Every operation is an explicit rounded one (no contraction is left to the
+// compiler), so the result does not depend on how the code around it is
+// unrolled or scheduled.
+__device__ __forceinline__ void chan_step(float &n, float &mean, float &m2, float nb, float mb,
+                                          float m2b) {
+  const float nab = __fadd_rn(n, nb);
+  const float delta = __fsub_rn(mb, mean);
+  const float wb = __fdiv_rn(nb, nab);
+  mean = fmaf(delta, wb, mean);
+  m2 = fmaf(__fmul_rn(delta, delta), __fmul_rn(n, wb), __fadd_rn(m2, m2b));
+  n = nab;
+}
+
 // Chan's pairwise merge of (n, mean, M2) summaries, FP32, down the warp; lane 0
 // ends with the warp's summary.
 __device__ __forceinline__ void warp_chan_merge(float &n, float &mean, float &m2) {
@@ -209,13 +261,8 @@ __device__ __forceinline__ void warp_chan_merge(float &n, float &mean, float &m2
     const float nb = __shfl_down_sync(kFullMask, n, off);
     const float mb = __shfl_down_sync(kFullMask, mean, off);
     const float m2b = __shfl_down_sync(kFullMask, m2, off);
-    const float nab = n + nb;
     if (nb > 0.0f) {
-      const float delta = mb - mean;
-      const float wb = __fdiv_rn(nb, nab);
-      mean = fmaf(delta, wb, mean);
-      m2 = m2 + m2b + delta * delta * (n * wb);
-      n = nab;
+      chan_step(n, mean, m2, nb, mb, m2b);
     }
   }
 }
@@ -237,18 +284,23 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 // turns them into (n, mean = s1/n, M2 = s2 - n (mean - K)^2) and merges that into
 // the lane's running summary (Chan's pairwise update); the warp then merges the
 // 32 lane summaries the same way.
-// Quints of one lane interleaved per loop step, per family (build-time knobs).
-#ifndef ZMC_QUINT_UNROLL
-#define ZMC_QUINT_UNROLL 1
-#endif
-#ifndef ZMC_QUINT_UNROLL_HARMONIC
-#define ZMC_QUINT_UNROLL_HARMONIC ZMC_QUINT_UNROLL
+// Quints of one lane unrolled per loop step.  Each family file is compiled once
+// per unroll (ZMC_FAM_UNROLL = 1, 2; build.py) into kernels of their own, and the
+// autotuner picks one per family.  The loop visits the same samples in the same
+// order; results agree within rounding (measured: the unrolled harmonic kernel
+// rounds some chunk sums differently, ~1e-7 relative), so a plan's results are
+// bit-identical for one choice of unroll.
+#ifndef ZMC_FAM_UNROLL
+#define ZMC_FAM_UNROLL 1
 #endif
 template <int FAM>
 struct QuintUnroll {
-  static constexpr int value =
-      FAM == ZMC_HARMONIC ? ZMC_QUINT_UNROLL_HARMONIC : ZMC_QUINT_UNROLL;
+  static constexpr int value = ZMC_FAM_UNROLL;
 };
+// The exported FamilyOps of a family file, named for its unroll: NAME##U1, NAME##U2.
+#define ZMC_PASTE2(a, b) a##b
+#define ZMC_PASTE(a, b) ZMC_PASTE2(a, b)
+#define ZMC_FAMILY_OPS(name) ZMC_PASTE(name, ZMC_PASTE(U, ZMC_FAM_UNROLL))
 // Quints per accumulation block: a lane's shifted sums never span more than
 // 5 * kBlockQuints samples, which bounds their rounding error for any chunk length.
 constexpr uint32_t kBlockQuints = 13;
@@ -273,6 +325,11 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
   for (uint32_t jb = 0; jb < Q; jb += kBlockQuints) {
     const uint32_t je = jb + kBlockQuints < Q ? jb + kBlockQuints : Q;
     float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    // families with a packed quint evaluation also sum full quints in packed
+    // pairs: samples (0, 1) and (2, 3) as pairs, 4 alone (the others keep the
+    // scalar sums, which need fewer registers)
+    constexpr bool kPackedSums = ZMC_PACKED_F32 && HasQuint<Eval<FAM, D, G>>::value;
+    float2 s1p = make_float2(0.0f, 0.0f), s2p = make_float2(0.0f, 0.0f), nK2;
     uint32_t cnt = 0;
 #pragma unroll QuintUnroll<FAM>::value
     for (uint32_t j = jb; j < je; ++j) {
@@ -284,10 +341,22 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
       else
         gen_quint<D>(quint0 + ql, sid, rk, r);
       float f[5];
-#pragma unroll
-      for (int t = 0; t < 5; ++t) f[t] = ev(r + t * D);
-      if (j == jb) K = f[0];
-      if (FAST) {
+      eval_quint<D>(ev, r, f);
+      if (j == jb) {
+        K = f[0];
+        nK2 = make_float2(-K, -K);
+      }
+      if (FAST && kPackedSums) {
+        const float2 f01 = make_float2(f[0], f[1]), f23 = make_float2(f[2], f[3]);
+        s1p = __fadd2_rn(s1p, f01);
+        s1p = __fadd2_rn(s1p, f23);
+        s1 += f[4];
+        const float2 d01 = __fadd2_rn(f01, nK2), d23 = __fadd2_rn(f23, nK2);
+        s2p = __ffma2_rn(d01, d01, s2p);
+        s2p = __ffma2_rn(d23, d23, s2p);
+        const float d4 = f[4] - K;
+        s2 = fmaf(d4, d4, s2);
+      } else if (FAST) {
         s1 += ((f[0] + f[1]) + (f[2] + f[3])) + f[4];
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
@@ -307,17 +376,16 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
         s1 += ((q[0] + q[1]) + (q[2] + q[3])) + q[4];
       }
     }
+    if (FAST && kPackedSums) {
+      s1 += s1p.x + s1p.y;
+      s2 += s2p.x + s2p.y;
+    }
     const float nb = FAST ? static_cast<float>(kQuint * (je - jb)) : static_cast<float>(cnt);
     if (nb > 0.0f) {
       const float mb = __fdiv_rn(s1, nb);
-      const float dk = mb - K;
-      const float m2b = fmaxf(fmaf(-nb * dk, dk, s2), 0.0f);
-      const float nab = n + nb;
-      const float delta = mb - mean;
-      const float wb = __fdiv_rn(nb, nab);
-      mean = fmaf(delta, wb, mean);
-      m2 = m2 + m2b + delta * delta * (n * wb);
-      n = nab;
+      const float dk = __fsub_rn(mb, K);
+      const float m2b = fmaxf(fmaf(__fmul_rn(-nb, dk), dk, s2), 0.0f);
+      chan_step(n, mean, m2, nb, mb, m2b);
     }
     if (!FAST && cnt < kQuint * (je - jb)) break;
   }

@@ -40,7 +40,7 @@ struct Eval<ZMC_ABSLIN, D, G> {
       l = fmaf(gl[i], __uint_as_float(vb), l);
     }
     const float s = __ll2float_rn(static_cast<long long>(acc)) + l;
-    return scale * fabsf(s);
+    return __fmul_rn(scale, fabsf(s));  // never contracted with the sums' f - K
   }
 };
 
@@ -66,6 +66,6 @@ __device__ void dispatch_eval<ZMC_ABSLIN>(const FnDev *fn, uint64_t s_begin, uin
 
 }  // namespace
 
-const FamilyOps kFamilyAbslin = family_ops<ZMC_ABSLIN>();
+const FamilyOps ZMC_FAMILY_OPS(kFamilyAbslin) = family_ops<ZMC_ABSLIN>();
 
 }  // namespace zmc

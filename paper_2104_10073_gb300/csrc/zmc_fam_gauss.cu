@@ -105,6 +105,6 @@ __device__ void dispatch_eval<ZMC_GAUSS>(const FnDev *fn, uint64_t s_begin, uint
 
 }  // namespace
 
-const FamilyOps kFamilyGauss = family_ops<ZMC_GAUSS>();
+const FamilyOps ZMC_FAMILY_OPS(kFamilyGauss) = family_ops<ZMC_GAUSS>();
 
 }  // namespace zmc

@@ -43,7 +43,7 @@ struct PolyCoeffEval {
         }
         qi = ph + pl;
       }
-      prod = (i == 0) ? qi : prod * qi;
+      prod = (i == 0) ? qi : __fmul_rn(prod, qi);  // never contracted with the sums
     }
     return prod;
   }
@@ -130,6 +130,6 @@ __device__ void dispatch_eval<ZMC_POLY>(const FnDev *fn, uint64_t s_begin, uint3
 
 }  // namespace
 
-const FamilyOps kFamilyPoly = family_ops<ZMC_POLY>();
+const FamilyOps ZMC_FAMILY_OPS(kFamilyPoly) = family_ops<ZMC_POLY>();
 
 }  // namespace zmc

@@ -146,12 +146,15 @@ struct FamilyOps {
                              cudaStream_t stream);
   int (*regs_per_thread)();  // registers of the family kernel as built (0 if unknown)
 };
-extern const FamilyOps kFamilyHarmonic, kFamilyAbslin, kFamilyGauss, kFamilyPoly;
+// Each family file is built once per quint-loop unroll (1 or 2): U1 and U2.
+extern const FamilyOps kFamilyHarmonicU1, kFamilyAbslinU1, kFamilyGaussU1, kFamilyPolyU1;
+extern const FamilyOps kFamilyHarmonicU2, kFamilyAbslinU2, kFamilyGaussU2, kFamilyPolyU2;
+constexpr int kMaxUnroll = 2;
 
 // Launch wrappers (zmc_kernels.cu, zmc_plain.cu).  All return the launch's
-// cudaError_t; an unknown family gives cudaErrorInvalidValue.
+// cudaError_t; an unknown family or unroll gives cudaErrorInvalidValue.
 cudaError_t launch_batched(int family, const Entry *entries, LaunchHdr *hdr, unsigned grid,
-                           unsigned block, cudaStream_t stream);
+                           unsigned block, cudaStream_t stream, int unroll = 1);
 cudaError_t launch_merge(const FnDev *const *fns, const LaunchHdr *hdr, unsigned grid,
                          cudaStream_t stream);
 cudaError_t launch_plain(const PlainFn &fn, double *block_rec, unsigned grid,
@@ -161,8 +164,8 @@ cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
                           cudaStream_t stream);
 cudaError_t launch_eval(int family, const FnDev *fn, uint64_t s_begin, uint32_t count,
                         float *out, cudaStream_t stream);
-int batched_max_blocks_per_sm(int family, int block);
-int batched_regs_per_thread(int family);
+int batched_max_blocks_per_sm(int family, int block, int unroll = 1);
+int batched_regs_per_thread(int family, int unroll = 1);
 unsigned plain_grid(const PlainFn &fn, int sms);
 #endif  // __CUDACC_RTC__
 

@@ -130,27 +130,20 @@ __global__ void __launch_bounds__(256, 2) zmc_philox_rate_kernel(uint32_t key0, 
   out[t] = acc;
 }
 
-const FamilyOps *ops_of(int family) {
-  switch (family) {
-    case ZMC_HARMONIC:
-      return &kFamilyHarmonic;
-    case ZMC_ABSLIN:
-      return &kFamilyAbslin;
-    case ZMC_GAUSS:
-      return &kFamilyGauss;
-    case ZMC_POLY:
-      return &kFamilyPoly;
-    default:
-      return nullptr;
-  }
+const FamilyOps *ops_of(int family, int unroll = 1) {
+  static const FamilyOps *const kOps[kMaxUnroll][4] = {
+      {&kFamilyHarmonicU1, &kFamilyAbslinU1, &kFamilyGaussU1, &kFamilyPolyU1},
+      {&kFamilyHarmonicU2, &kFamilyAbslinU2, &kFamilyGaussU2, &kFamilyPolyU2}};
+  if (family < 0 || family > ZMC_POLY || unroll < 1 || unroll > kMaxUnroll) return nullptr;
+  return kOps[unroll - 1][family];
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- launch wrappers
 cudaError_t launch_batched(int family, const Entry *entries, LaunchHdr *hdr, unsigned grid,
-                           unsigned block, cudaStream_t stream) {
-  const FamilyOps *ops = ops_of(family);
+                           unsigned block, cudaStream_t stream, int unroll) {
+  const FamilyOps *ops = ops_of(family, unroll);
   return ops ? ops->launch_batched(entries, hdr, grid, block, stream) : cudaErrorInvalidValue;
 }
 
@@ -160,13 +153,13 @@ cudaError_t launch_merge(const FnDev *const *fns, const LaunchHdr *hdr, unsigned
   return cudaGetLastError();
 }
 
-int batched_max_blocks_per_sm(int family, int block) {
-  const FamilyOps *ops = ops_of(family);
+int batched_max_blocks_per_sm(int family, int block, int unroll) {
+  const FamilyOps *ops = ops_of(family, unroll);
   return ops ? ops->max_blocks_per_sm(block) : 0;
 }
 
-int batched_regs_per_thread(int family) {
-  const FamilyOps *ops = ops_of(family);
+int batched_regs_per_thread(int family, int unroll) {
+  const FamilyOps *ops = ops_of(family, unroll);
   return ops ? ops->regs_per_thread() : 0;
 }
 

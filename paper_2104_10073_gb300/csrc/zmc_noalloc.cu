@@ -15,16 +15,22 @@
 // device is not acceptable, or a caller that cannot afford zmc_create's arena.
 //
 // Costs and rules:
-//   * the array below (ZMC_NOALLOC_SCRATCH_BYTES) is reserved on every GPU that
-//     loads the library, until the process exits;
+//   * the array below (ZMC_NOALLOC_SCRATCH_BYTES) is reserved on a device once
+//     the library's device code is loaded there (with CUDA's lazy module
+//     loading, at the latest on the first call on that device) and stays
+//     reserved until the process exits;
+//   * the tables are uploaded from a static (pageable) host buffer; before a
+//     call overwrites that buffer it waits until the previous call's upload has
+//     completed on the GPU (an event recorded after the upload), so a call may
+//     block until the previous call's stream has reached its upload;
 //   * every call uses the same array and it keeps the last call's contents;
 //     the call re-uploads the tables and zeroes the work counters itself, and
 //     every partial-sum record is written before it is read;
 //   * calls whose GPU work overlaps (different streams, or different host
 //     threads on one stream without ordering) race on the array: order them;
 //   * the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture.
+//     (cudaGetSymbolAddress) and creates the upload event, with that device
+//     current; make that first call before any stream capture.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -53,6 +59,8 @@ alignas(256) unsigned char g_host_stage[kHostBytes];
 uint32_t g_order[kMaxFns];
 std::mutex g_mu;
 unsigned char *g_scratch_dev[kMaxDevices];  // device address of the array, per device
+cudaEvent_t g_upload_ev[kMaxDevices];       // recorded after each call's table upload
+cudaEvent_t g_last_upload = nullptr;        // the event of the last call, any device
 
 }  // namespace
 
@@ -76,6 +84,13 @@ extern "C" zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_
       return set_error(ZMC_ECUDA, "scratch address lookup: %s", cudaGetErrorString(e));
     g_scratch_dev[dev] = static_cast<unsigned char *>(p);
   }
+  if (!g_upload_ev[dev]) {
+    e = cudaEventCreateWithFlags(&g_upload_ev[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      g_upload_ev[dev] = nullptr;
+      return set_error(ZMC_ECUDA, "upload event: %s", cudaGetErrorString(e));
+    }
+  }
   unsigned char *dbase = g_scratch_dev[dev];
 
   // layout for this call
@@ -97,6 +112,16 @@ extern "C" zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_
                      static_cast<unsigned long long>(need), kScratchBytes,
                      static_cast<unsigned long long>((kScratchBytes - off_rec) / sizeof(float2) *
                                                      chunk));
+
+  // the previous call's upload must have read the staging buffer before it is
+  // rewritten (a pageable asynchronous copy need not have consumed its source
+  // when cudaMemcpyAsync returns)
+  if (g_last_upload) {
+    e = cudaEventSynchronize(g_last_upload);
+    if (e != cudaSuccess)
+      return set_error(ZMC_ECUDA, "previous upload: %s", cudaGetErrorString(e));
+    g_last_upload = nullptr;
+  }
 
   // host tables
   LaunchHdr *hdr = reinterpret_cast<LaunchHdr *>(g_host_stage + kOffHdr);
@@ -149,9 +174,15 @@ extern "C" zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return set_error(ZMC_ECUDA, "device query: %s", cudaGetErrorString(e));
   cudaStream_t str = static_cast<cudaStream_t>(stream);
-  // pageable source: the tables are staged by the driver before this returns
   e = cudaMemcpyAsync(dbase, g_host_stage, off_rec, cudaMemcpyHostToDevice, str);
   if (e != cudaSuccess) return set_error(ZMC_ECUDA, "table upload: %s", cudaGetErrorString(e));
+  e = cudaEventRecord(g_upload_ev[dev], str);
+  if (e != cudaSuccess) {
+    // the copy may still read the staging buffer: wait for it here instead
+    cudaStreamSynchronize(str);
+    return set_error(ZMC_ECUDA, "upload event: %s", cudaGetErrorString(e));
+  }
+  g_last_upload = g_upload_ev[dev];
   for (int f = 0; f < 4; ++f) {
     const uint64_t items = hdr->item_end[f] - hdr->item_begin[f];
     if (items == 0) continue;

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <limits>
 #include <numeric>
+#include <sstream>
 
 #include "zmc_runtime.h"
 
@@ -411,9 +412,10 @@ zmc_status ensure_stage(zmc_ctx *ctx, size_t bytes) {
   return ZMC_OK;
 }
 
-unsigned grid_for(const zmc_ctx *ctx, int family, unsigned block, unsigned bps, uint64_t items) {
+unsigned grid_for(const zmc_ctx *ctx, int family, unsigned block, unsigned bps, uint64_t items,
+                  int unroll) {
   const unsigned warps_per_block = block / 32;
-  const int maxb = batched_max_blocks_per_sm(family, static_cast<int>(block));
+  const int maxb = batched_max_blocks_per_sm(family, static_cast<int>(block), unroll);
   if (bps == 0 || bps > static_cast<unsigned>(std::max(maxb, 1)))
     bps = static_cast<unsigned>(std::max(maxb, 1));
   const uint64_t full = static_cast<uint64_t>(ctx->sms) * bps;
@@ -421,8 +423,8 @@ unsigned grid_for(const zmc_ctx *ctx, int family, unsigned block, unsigned bps, 
   return static_cast<unsigned>(std::max<uint64_t>(1, std::min(full, need)));
 }
 
-unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items) {
-  return grid_for(ctx, family, ctx->shape.block, ctx->shape.blocks_per_sm[family], items);
+unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items, int unroll) {
+  return grid_for(ctx, family, ctx->shape.block, ctx->shape.blocks_per_sm[family], items, unroll);
 }
 
 cudaError_t FamilyFork::init() {
@@ -447,20 +449,23 @@ void FamilyFork::destroy() {
 
 cudaError_t launch_families(FamilyFork &ff, const Entry *entries, LaunchHdr *hdr,
                             const unsigned *grid, const unsigned *block, const bool *present,
-                            cudaStream_t main) {
+                            cudaStream_t main, const unsigned *unroll) {
   int fams[4], n = 0;
   for (int f = 0; f < 4; ++f)
     if (present[f]) fams[n++] = f;
+  auto launch = [&](int f, cudaStream_t s) {
+    return launch_batched(f, entries, hdr, grid[f], block[f], s,
+                          unroll ? static_cast<int>(unroll[f]) : 1);
+  };
   if (n == 0) return cudaSuccess;
-  if (n == 1 || !ff.fork) return launch_batched(fams[0], entries, hdr, grid[fams[0]], block[fams[0]], main);
+  if (n == 1 || !ff.fork) return launch(fams[0], main);
   cudaError_t e = cudaEventRecord(ff.fork, main);
   for (int k = 1; k < n && e == cudaSuccess; ++k) {
     e = cudaStreamWaitEvent(ff.side[k - 1], ff.fork, 0);
-    if (e == cudaSuccess)
-      e = launch_batched(fams[k], entries, hdr, grid[fams[k]], block[fams[k]], ff.side[k - 1]);
+    if (e == cudaSuccess) e = launch(fams[k], ff.side[k - 1]);
     if (e == cudaSuccess) e = cudaEventRecord(ff.join[k - 1], ff.side[k - 1]);
   }
-  if (e == cudaSuccess) e = launch_batched(fams[0], entries, hdr, grid[fams[0]], block[fams[0]], main);
+  if (e == cudaSuccess) e = launch(fams[0], main);
   for (int k = 1; k < n && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(main, ff.join[k - 1], 0);
   return e;
 }
@@ -489,6 +494,9 @@ struct zmc_plan {
   uint64_t n_chunks = 0, n_samples = 0;
   uint64_t fam_items[4] = {0, 0, 0, 0};
   bool ranged = false;  // built by zmc_integrate_moments (no plain form)
+  uint32_t quints = 0;  // chunk = 160 * quints samples
+  unsigned unroll[4] = {1, 1, 1, 1};  // quint-loop unroll of each family kernel
+  int chunk_source = 0;  // chunk length and unroll: 0 default, 1 measured, 2 cached
   unsigned grid[4] = {0, 0, 0, 0};
   unsigned block[4] = {256, 256, 256, 256};
   int tune_source[4] = {0, 0, 0, 0};  // 0 default, 1 measured, 2 from the cache
@@ -530,12 +538,13 @@ zmc_status plan_autotune(zmc_plan *plan) {
   zmc_status st = ZMC_OK;
   for (int f = 0; f < 4 && st == ZMC_OK; ++f) {
     if (plan->fam_items[f] == 0) continue;
-    const std::string key = tune_key(ctx, f, plan->dominant_dim[f]);
+    const int U = static_cast<int>(plan->unroll[f]);
+    const std::string key = tune_key(ctx, f, plan->dominant_dim[f], plan->quints, U);
     auto hit = ctx->tune_cache.find(key);
     if (hit != ctx->tune_cache.end()) {
       plan->block[f] = hit->second.block;
       plan->grid[f] = grid_for(ctx, f, hit->second.block, hit->second.blocks_per_sm,
-                               plan->fam_items[f]);
+                               plan->fam_items[f], U);
       plan->tune_source[f] = 2;
       continue;
     }
@@ -548,14 +557,15 @@ zmc_status plan_autotune(zmc_plan *plan) {
     TuneChoice best;
     best.ms = 1e30f;
     for (unsigned block : {128u, 256u}) {
-      const int maxb = batched_max_blocks_per_sm(f, static_cast<int>(block));
+      const int maxb = batched_max_blocks_per_sm(f, static_cast<int>(block), U);
       for (int bps = 1; bps <= maxb && st == ZMC_OK; ++bps) {
-        const unsigned grid = grid_for(ctx, f, block, static_cast<unsigned>(bps), slice);
+        const unsigned grid = grid_for(ctx, f, block, static_cast<unsigned>(bps), slice, U);
         float ms_best = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
           cudaError_t e = cudaMemcpyAsync(plan->d_hdr, &th, sizeof th, cudaMemcpyHostToDevice, str);
           if (e == cudaSuccess) e = cudaEventRecord(e0, str);
-          if (e == cudaSuccess) e = launch_batched(f, plan->d_entries, plan->d_hdr, grid, block, str);
+          if (e == cudaSuccess)
+            e = launch_batched(f, plan->d_entries, plan->d_hdr, grid, block, str, U);
           if (e == cudaSuccess) e = cudaEventRecord(e1, str);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
           float ms = 0.0f;
@@ -575,7 +585,7 @@ zmc_status plan_autotune(zmc_plan *plan) {
     }
     if (st != ZMC_OK) break;
     plan->block[f] = best.block;
-    plan->grid[f] = grid_for(ctx, f, best.block, best.blocks_per_sm, plan->fam_items[f]);
+    plan->grid[f] = grid_for(ctx, f, best.block, best.blocks_per_sm, plan->fam_items[f], U);
     plan->tune_source[f] = 1;
     tune_cache_store(ctx, key, best);
   }
@@ -589,9 +599,153 @@ zmc_status plan_autotune(zmc_plan *plan) {
   return ZMC_OK;
 }
 
-// ranges: optional [s_begin[i], s_end[i]) sample ranges (moments output).
+// A fixed chunk length and unroll for plan_build (the chunk tuner's trial plans).
+struct PlanChoice {
+  uint32_t quints;
+  unsigned unroll[4];
+};
+
 zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out,
-                      const uint64_t *s_begin = nullptr, const uint64_t *s_end = nullptr) {
+                      const uint64_t *s_begin = nullptr, const uint64_t *s_end = nullptr,
+                      const PlanChoice *force = nullptr);
+void plan_free(zmc_plan *plan);
+
+// The key of a table's shape class for the chunk tuner: the GPU, the families
+// present with their dominant dimension and kernels' registers, and the
+// table's size (log2 of the rows and of the mean samples per row).
+std::string chunk_tune_key(const zmc_ctx *ctx, const zmc_desc *desc, size_t n) {
+  double dim_samples[4][kMaxDim + 1] = {{0}};
+  double total = 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    dim_samples[desc[i].family][desc[i].dim] += static_cast<double>(desc[i].n_samples);
+    total += static_cast<double>(desc[i].n_samples);
+  }
+  std::ostringstream k;
+  k << "chunk|" << ctx->gpu_name << '|' << ctx->sms;
+  for (int f = 0; f < 4; ++f) {
+    int best = 0;
+    for (int d = 1; d <= kMaxDim; ++d)
+      if (dim_samples[f][d] > dim_samples[f][best]) best = d;
+    if (best == 0) continue;
+    k << "|f" << f << 'd' << best << 'r' << ctx->kernel_regs[0][f] << '/'
+      << ctx->kernel_regs[1][f];
+  }
+  k << "|n" << static_cast<int>(std::floor(std::log2(static_cast<double>(n)))) << "|s"
+    << static_cast<int>(std::floor(std::log2(std::max(1.0, total / static_cast<double>(n)))));
+  return k.str();
+}
+
+// Device time of one family kernel of a plan draining all of its items: the
+// best of two launches after a warm-up (milliseconds).
+zmc_status time_family(zmc_plan *plan, int f, int unroll, cudaEvent_t e0, cudaEvent_t e1,
+                       float *ms_out) {
+  zmc_ctx *ctx = plan->ctx;
+  cudaStream_t str = ctx->stream;
+  const unsigned grid = grid_for(ctx, f, ctx->shape.block, ctx->shape.blocks_per_sm[f],
+                                 plan->fam_items[f], unroll);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaError_t e = cudaMemsetAsync(plan->d_hdr, 0, sizeof(plan->d_hdr->counter), str);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, str);
+    if (e == cudaSuccess)
+      e = launch_batched(f, plan->d_entries, plan->d_hdr, grid, ctx->shape.block, str, unroll);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, str);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "chunk autotune");
+    if (rep > 0) best = std::min(best, ms);
+  }
+  *ms_out = best;
+  return ZMC_OK;
+}
+
+// Samples of the table subset the chunk tuner times each candidate on.
+constexpr double kTrialSamples = 2147483648.0;
+
+// Chunk tuner: the chunk length (kTuneQuints) and per-family unroll under which
+// a bounded subset of the table's rows (every k-th row, whole rows) samples
+// fastest, or the cached choice for the table's shape class.  Each candidate
+// chunk length builds a trial plan of the subset; each family kernel present is
+// timed alone at both unrolls.  *source: 1 measured, 2 cached, 0 left at the
+// defaults (a trial plan did not fit the arena).
+zmc_status choose_chunk(zmc_ctx *ctx, const zmc_desc *desc, size_t n, PlanChoice *choice,
+                        int *source) {
+  const std::string key = chunk_tune_key(ctx, desc, n);
+  auto hit = ctx->tune_cache.find(key);
+  if (hit != ctx->tune_cache.end()) {
+    choice->quints = hit->second.quints;
+    for (int f = 0; f < 4; ++f) choice->unroll[f] = hit->second.unroll[f];
+    *source = 2;
+    return ZMC_OK;
+  }
+  double total = 0.0;
+  for (size_t i = 0; i < n; ++i) total += static_cast<double>(desc[i].n_samples);
+  const size_t stride =
+      total <= kTrialSamples ? 1 : static_cast<size_t>(std::ceil(total / kTrialSamples));
+  std::vector<zmc_desc> sub;
+  for (size_t i = 0; i < n; i += stride) sub.push_back(desc[i]);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ZMC_CUDA(ctx, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ctx_cuda_fail(ctx, ce, "chunk autotune");
+  }
+  zmc_status st = ZMC_OK;
+  float best_total = 1e30f;
+  TuneChoice best;
+  for (uint32_t q : kTuneQuints) {
+    PlanChoice trial_choice{q, {1, 1, 1, 1}};
+    zmc_plan *trial = nullptr;
+    st = plan_build(ctx, sub.data(), sub.size(), &trial, nullptr, nullptr, &trial_choice);
+    if (st == ZMC_ENOMEM) {  // the arena cannot hold this trial: skip the candidate
+      st = ZMC_OK;
+      continue;
+    }
+    if (st != ZMC_OK) break;
+    float sum = 0.0f;
+    unsigned u_best[4] = {1, 1, 1, 1};
+    for (int f = 0; f < 4 && st == ZMC_OK; ++f) {
+      if (trial->fam_items[f] == 0) continue;
+      float t_best = 1e30f;
+      for (int u = 1; u <= kMaxUnroll && st == ZMC_OK; ++u) {
+        float ms = 0.0f;
+        st = time_family(trial, f, u, e0, e1, &ms);
+        if (ms < t_best) {
+          t_best = ms;
+          u_best[f] = static_cast<unsigned>(u);
+        }
+      }
+      sum += t_best;
+    }
+    plan_free(trial);
+    if (st != ZMC_OK) break;
+    if (sum < best_total) {
+      best_total = sum;
+      best.quints = q;
+      for (int f = 0; f < 4; ++f) best.unroll[f] = u_best[f];
+      best.ms = sum;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ZMC_OK) return st;
+  if (best.quints == 0) {  // no candidate fitted
+    *source = 0;
+    return ZMC_OK;
+  }
+  tune_cache_store(ctx, key, best);
+  choice->quints = best.quints;
+  for (int f = 0; f < 4; ++f) choice->unroll[f] = best.unroll[f];
+  *source = 1;
+  return ZMC_OK;
+}
+
+// ranges: optional [s_begin[i], s_end[i]) sample ranges (moments output).
+// force: a fixed chunk length and unroll, no autotuning (trial plans).
+zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out,
+                      const uint64_t *s_begin, const uint64_t *s_end, const PlanChoice *force) {
   if (!desc || !out || n == 0) return set_error(ZMC_EINVAL, "need n >= 1 descriptors");
   if (n >= (1u << 31)) return set_error(ZMC_EINVAL, "too many descriptors");
   auto plan = std::make_unique<zmc_plan>();
@@ -628,7 +782,18 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
       fns[i].out_mode = 1;
     }
   }
-  const uint64_t chunk = chunk_samples_of(ctx->quints_per_lane);
+  // chunk length and unroll: fixed by the caller, chosen by the chunk tuner, or
+  // the context's chunk length with unroll 1
+  PlanChoice choice{ctx->quints_per_lane, {1, 1, 1, 1}};
+  if (force) {
+    choice = *force;
+  } else if ((ctx->autotune & ZMC_TUNE_CHUNK) && !s_begin) {
+    const zmc_status cs = choose_chunk(ctx, desc, n, &choice, &plan->chunk_source);
+    if (cs != ZMC_OK) return cs;
+  }
+  plan->quints = choice.quints;
+  for (int f = 0; f < 4; ++f) plan->unroll[f] = choice.unroll[f];
+  const uint64_t chunk = chunk_samples_of(plan->quints);
   std::vector<uint64_t> nchunk(n), rec_off(n);
   uint64_t total = 0, samples = 0;
   for (size_t i = 0; i < n; ++i) {
@@ -695,11 +860,11 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
   }
   h.n_entries = static_cast<uint32_t>(n);
   h.n_merge = static_cast<uint32_t>(n);
-  h.quints_per_lane = ctx->quints_per_lane;
+  h.quints_per_lane = plan->quints;
   for (int f = 0; f < 4; ++f) {
     plan->fam_items[f] = h.item_end[f] - h.item_begin[f];
     plan->block[f] = ctx->shape.block;
-    plan->grid[f] = family_grid(ctx, f, plan->fam_items[f]);
+    plan->grid[f] = family_grid(ctx, f, plan->fam_items[f], static_cast<int>(plan->unroll[f]));
   }
   {
     double dim_samples[4][kMaxDim + 1] = {{0}};
@@ -742,7 +907,7 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
     plan->release_all();
     return ctx_cuda_fail(ctx, e, "plan upload");
   }
-  if (ctx->autotune) {
+  if ((ctx->autotune & ZMC_TUNE_GEOMETRY) && !force) {
     zmc_status ts = plan_autotune(plan.get());
     if (ts != ZMC_OK) {
       plan->release_all();
@@ -761,7 +926,7 @@ zmc_status plan_enqueue(zmc_plan *plan, uint32_t stages) {
     bool present[4];
     for (int f = 0; f < 4; ++f) present[f] = plan->fam_items[f] > 0;
     ZMC_CUDA(ctx, launch_families(ctx->fork, plan->d_entries, plan->d_hdr, plan->grid,
-                                  plan->block, present, str));
+                                  plan->block, present, str, plan->unroll));
   }
   if (stages & ZMC_STAGE_MERGE) {
     const unsigned grid = static_cast<unsigned>(
@@ -884,6 +1049,8 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   // at 4096, which measured lower job latency under load
   if (opt.quints_per_lane == 0) opt.quints_per_lane = opt.serving ? 26 : 104;
   if (opt.quints_per_lane > 1024) return set_error(ZMC_EINVAL, "quints_per_lane above 1024");
+  if (opt.autotune & ~(ZMC_TUNE_GEOMETRY | ZMC_TUNE_CHUNK))
+    return set_error(ZMC_EINVAL, "unknown autotune flags 0x%x", opt.autotune);
   if (opt.arena && (reinterpret_cast<uintptr_t>(opt.arena) & 255))
     return set_error(ZMC_EINVAL, "arena must be 256-byte aligned");
   int ndev = 0;
@@ -923,12 +1090,12 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   ctx->arena.init(ctx->arena_base, opt.mem_budget_bytes);
   ctx->quints_per_lane = opt.quints_per_lane;
   ctx->max_chunks_per_iter = opt.max_chunks_per_iter;
-  ctx->autotune = opt.autotune != 0;
+  ctx->autotune = opt.autotune;
   if (opt.tune_cache_path) ctx->tune_cache_path = opt.tune_cache_path;
   tune_cache_load(ctx.get());
   for (int f = 0; f < 4; ++f) {
     ctx->max_blocks_per_sm[f] = batched_max_blocks_per_sm(f, 256);
-    ctx->kernel_regs[f] = batched_regs_per_thread(f);
+    for (int u = 1; u <= kMaxUnroll; ++u) ctx->kernel_regs[u - 1][f] = batched_regs_per_thread(f, u);
   }
   e = ctx->fork.init();
   if (e != cudaSuccess) {
@@ -1035,8 +1202,11 @@ zmc_status zmc_plan_info_get(const zmc_plan *plan, zmc_plan_info *out) {
     out->family_block[f] = plan->fam_items[f] ? plan->block[f] : 0;
     out->tune_source[f] = plan->tune_source[f];
   }
-  out->quints_per_lane = plan->ctx->quints_per_lane;
+  out->quints_per_lane = plan->quints;
   out->sms = static_cast<uint32_t>(plan->ctx->sms);
+  for (int f = 0; f < 4; ++f) out->family_unroll[f] = plan->unroll[f];
+  out->chunk_tune_source = plan->chunk_source;
+  out->reserved = 0;
   return ZMC_OK;
 }
 

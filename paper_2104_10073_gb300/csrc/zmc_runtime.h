@@ -51,12 +51,16 @@ struct LaunchShape {
   unsigned blocks_per_sm[4] = {0, 0, 0, 0};  // 0 -> occupancy maximum
 };
 
-// One autotuned geometry (zmc_tune.cpp).
+// One autotuner result (zmc_tune.cpp): a family kernel's launch geometry, or
+// (quints > 0) a table shape class's chunk length and per-family unroll.
 struct TuneChoice {
   unsigned block = 256;
   unsigned blocks_per_sm = 0;
+  unsigned quints = 0;
+  unsigned unroll[4] = {1, 1, 1, 1};
   float ms = 0.0f;
 };
+constexpr uint32_t kTuneQuints[] = {26, 52, 104, 208};  // chunk lengths the tuner tries
 
 struct Job;
 
@@ -81,7 +85,7 @@ struct FamilyFork {
 // concurrently when more than one is present.
 cudaError_t launch_families(FamilyFork &ff, const Entry *entries, LaunchHdr *hdr,
                             const unsigned *grid, const unsigned *block, const bool *present,
-                            cudaStream_t main);
+                            cudaStream_t main, const unsigned *unroll = nullptr);
 // The generator-only kernel (zmc_kernels.cu): grid x 256 threads, per_thread
 // Philox blocks each (a multiple of 4), one folded word per thread into out.
 cudaError_t launch_philox_rate(uint32_t per_thread, unsigned grid, uint32_t *out,
@@ -100,11 +104,11 @@ struct zmc_ctx {
   zmc::Arena arena;
   uint32_t quints_per_lane = 16;
   uint32_t max_chunks_per_iter = 0;
-  bool autotune = false;
+  uint32_t autotune = 0;  // ZMC_TUNE_* flags
   std::string tune_cache_path;
   zmc::LaunchShape shape;
   int max_blocks_per_sm[4] = {0, 0, 0, 0};
-  int kernel_regs[4] = {0, 0, 0, 0};  // registers per thread of each family kernel
+  int kernel_regs[zmc::kMaxUnroll][4] = {};  // registers per thread of each family kernel
   std::map<std::string, zmc::TuneChoice> tune_cache;  // autotuner results by key
   std::atomic<bool> poisoned{false};
   std::recursive_mutex api_mu;  // serialises API calls that use the stream
@@ -121,9 +125,10 @@ struct zmc_ctx {
 namespace zmc {
 zmc_status ctx_cuda_fail(zmc_ctx *ctx, cudaError_t err, const char *what);
 zmc_status ensure_stage(zmc_ctx *ctx, size_t bytes);
-unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items);
-unsigned grid_for(const zmc_ctx *ctx, int family, unsigned block, unsigned bps, uint64_t items);
-std::string tune_key(const zmc_ctx *ctx, int family, int dim);
+unsigned family_grid(const zmc_ctx *ctx, int family, uint64_t items, int unroll = 1);
+unsigned grid_for(const zmc_ctx *ctx, int family, unsigned block, unsigned bps, uint64_t items,
+                  int unroll = 1);
+std::string tune_key(const zmc_ctx *ctx, int family, int dim, uint32_t quints, int unroll);
 void tune_cache_load(zmc_ctx *ctx);
 void tune_cache_store(zmc_ctx *ctx, const std::string &key, const TuneChoice &c);
 }  // namespace zmc

@@ -352,6 +352,7 @@ void scheduler_loop(ServingState *S) {
     for (auto &j : S->live)
       if (j->state == JobState::kRunning && j->chunks_issued < j->chunks_total) active.push_back(j);
     uint32_t n_entries = 0;
+    uint64_t jobs_in_iter = 0;  // jobs with work items in this launch
     // Each job with work left gets budget / active chunks, but at least
     // kMinQuantum: with many live jobs, runs of a few chunks would turn every work
     // item into an entry-table search.  Jobs are visited oldest first.
@@ -361,6 +362,7 @@ void scheduler_loop(ServingState *S) {
       std::vector<std::shared_ptr<ServJob>> still;
       for (auto &j : active) {
         uint64_t take = std::min<uint64_t>(share, budget);
+        if (j->last_seq != seq && take > 0) ++jobs_in_iter;
         while (take > 0 && j->cursor < j->n && n_entries < S->max_entries) {
           const size_t i = j->cursor;
           const uint64_t left = j->nchunk[i] - j->next_chunk[i];
@@ -482,6 +484,8 @@ void scheduler_loop(ServingState *S) {
                                  }),
                   S->live.end());
     S->stats.iterations++;
+    if (jobs_in_iter >= 2) S->stats.shared_iterations++;
+    S->stats.max_jobs_per_iter = std::max(S->stats.max_jobs_per_iter, jobs_in_iter);
     lk.unlock();
 
     // ---- enqueue: upload tables, replay the graph, copy merged results back

@@ -45,7 +45,7 @@ struct Eval<ZMC_USER, D, G> {
     float x[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) x[i] = fmaf(wd[i], unit_v(r[i]) - 1.0f, lo[i]);  // u exact
-    return S * UserFn<G>::f(x, p);
+    return __fmul_rn(S, UserFn<G>::f(x, p));  // never contracted with the sums' f - K
   }
 };
 #else

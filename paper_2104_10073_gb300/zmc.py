@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_EAGAIN",
                 4: "ZMC_ETIMEOUT", 5: "ZMC_ECUDA", 6: "ZMC_ENOTFOUND", 7: "ZMC_ECLOSED",
                 8: "ZMC_ENOSYS"}
 ZMC_STAGE_SAMPLE, ZMC_STAGE_MERGE, ZMC_STAGE_ALL = 1, 2, 3
+ZMC_TUNE_GEOMETRY, ZMC_TUNE_CHUNK = 1, 2  # zmc_options.autotune flags
 ZMC_USER = 4
 DEFAULT_QUINTS_PER_LANE = 104  # the library's default chunk: 160 x 104 = 16640 samples
 SERVING_QUINTS_PER_LANE = 26  # ... and for a serving context: 4160 samples
@@ -54,7 +55,9 @@ class zmc_plan_info(ctypes.Structure):
                 ("n_samples", ctypes.c_uint64), ("grid", ctypes.c_uint32),
                 ("block", ctypes.c_uint32), ("quints_per_lane", ctypes.c_uint32),
                 ("sms", ctypes.c_uint32), ("family_grid", ctypes.c_uint32 * 4),
-                ("family_block", ctypes.c_uint32 * 4), ("tune_source", ctypes.c_int32 * 4)]
+                ("family_block", ctypes.c_uint32 * 4), ("tune_source", ctypes.c_int32 * 4),
+                ("family_unroll", ctypes.c_uint32 * 4), ("chunk_tune_source", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class zmc_normal_opts(ctypes.Structure):
@@ -74,7 +77,8 @@ class zmc_normal_result(ctypes.Structure):
 class zmc_serving_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "completed", "cancelled", "queued", "running", "iterations",
-        "samples_done", "arena_used_bytes", "arena_bytes")]
+        "samples_done", "arena_used_bytes", "arena_bytes", "shared_iterations",
+        "max_jobs_per_iter")]
 
 
 class ZmcError(RuntimeError):
@@ -520,7 +524,7 @@ class Context:
     def __init__(self, arena_bytes: int = 1 << 30, device: int = 0, stream=None,
                  serving: bool = False, quints_per_lane: int = 0,
                  max_chunks_per_iter: int = 0,
-                 use_torch_memory: bool = True, autotune: bool = False,
+                 use_torch_memory: bool = True, autotune: bool | int = False,
                  tune_cache_path: str | None = None):
         import torch
 
@@ -534,7 +538,9 @@ class Context:
         opt.serving = 1 if serving else 0
         opt.quints_per_lane = quints_per_lane
         opt.max_chunks_per_iter = max_chunks_per_iter
-        opt.autotune = 1 if autotune else 0
+        # True: launch geometry only; an int: ZMC_TUNE_* flags
+        opt.autotune = (ZMC_TUNE_GEOMETRY if autotune is True
+                        else int(autotune) if autotune else 0)
         self._tune_path = tune_cache_path.encode() if tune_cache_path else None
         opt.tune_cache_path = self._tune_path
         self.arena = None

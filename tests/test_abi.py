@@ -67,6 +67,7 @@ def _bad(mutator):
     ("nan_box", lambda r: r["hi"].__setitem__(0, np.nan)),
     ("inf_param", lambda r: r["p"].__setitem__(3, np.inf)),
     ("huge_phase", lambda r: r["p"].__setitem__(2, 1e9)),
+    ("nsamples_above_2p62", lambda r: r.__setitem__("n_samples", 2**62 + 1)),
 ])
 def test_validation_rejects(lib, name, mut):
     st, bad, msg = _bad(mut)
@@ -133,3 +134,29 @@ def test_validation_reports_the_first_bad_row_of_a_large_table(lib):
     t["n_samples"][3777] = 10
     st, bad, msg = zmc.zmc_validate(t)
     assert st == zmc.ZMC_EINVAL and bad == 4500 and "dim" in msg
+
+
+def test_validation_rules_of_the_fp32_constants(lib):
+    """The rules zmc.h lists beside zmc_desc for the derived FP32 constants: each
+    is reported with its own reason."""
+    def one(fill):
+        t = W.empty(1)
+        fill(t[0])
+        return zmc.zmc_validate(t)
+
+    # a harmonic span of more than 2^20 turns in one dimension
+    st, _, msg = one(lambda r: W.harmonic(r, 1.0, 1.0, [2 * np.pi * 2**20 * 1.01], [0.0], [1.0], 10))
+    assert st == zmc.ZMC_EINVAL and "2^20" in msg
+    # just inside it is accepted
+    st, _, _ = one(lambda r: W.harmonic(r, 1.0, 1.0, [2 * np.pi * 2**20 * 0.99], [0.0], [1.0], 10))
+    assert st == zmc.ZMC_OK
+    # a phase offset k.lo beyond 4e15 turns
+    st, _, msg = one(lambda r: W.harmonic(r, 1.0, 1.0, [1.0], [1e17], [1e17 + 64.0], 10))
+    assert st == zmc.ZMC_EINVAL and "phase" in msg
+    # amplitudes whose scaled FP32 constants overflow (the scale stops at 2^-100)
+    for fill in (lambda r: W.harmonic(r, 1e300, 0.0, [1.0], [0.0], [1.0], 10),
+                 lambda r: W.gauss(r, 1e300, 0.5, [0.5], [0.0], [1.0], 10),
+                 lambda r: W.abslin(r, 1e300, [1.0], [0.0], [1.0], 10),
+                 lambda r: W.poly(r, [[1e300, 1.0]], [0.0], [1.0], 10)):
+        st, _, msg = one(fill)
+        assert st == zmc.ZMC_EINVAL and "range" in msg, msg

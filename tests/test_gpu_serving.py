@@ -42,6 +42,9 @@ def test_results_same_alone_and_mixed(sctx, sq_ctx):
         st, res = zmc.zmc_poll(sctx.handle, jid, len(t), wait_ms=-1)
         assert st == zmc.ZMC_OK
         alone.append(res)
+    # one job at a time never shares a launch
+    assert zmc.zmc_serving_stats_get(sctx.handle)["max_jobs_per_iter"] == 1
+    before = zmc.zmc_serving_stats_get(sctx.handle)
     # mixed: all submitted at once, interleaved over shared persistent launches
     ids = [zmc.zmc_submit(sctx.handle, t) for t in jobs]
     for t, jid, a in zip(jobs, ids, alone):
@@ -49,6 +52,13 @@ def test_results_same_alone_and_mixed(sctx, sq_ctx):
         assert st == zmc.ZMC_OK
         assert np.array_equal(res["estimate"], a["estimate"])
         assert np.array_equal(res["stderr"], a["stderr"], equal_nan=True)
+        assert np.array_equal(res["n"], a["n"]) and np.array_equal(res["status"], a["status"])
+    after = zmc.zmc_serving_stats_get(sctx.handle)
+    # the mixed phase really shared launches: work items of several jobs ran in
+    # the same persistent launch (a scheduler that ran the jobs one after the
+    # other would leave both counters where the alone phase left them)
+    assert after["shared_iterations"] - before["shared_iterations"] >= 1
+    assert after["max_jobs_per_iter"] >= 4
     # and the same as the blocking batched call with the same chunk length, and
     # the oracle
     for t, a in zip(jobs[:4], alone[:4]):

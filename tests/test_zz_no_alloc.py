@@ -4,11 +4,15 @@ Some callers may not allocate device memory at the moment they need a result
 (a framework whose pool owns the device memory, a latency-bound loop, code
 without a library context).  The no-allocation entry point keeps all of its
 working memory in a fixed array inside the library; the caller passes only the
-descriptor table and a device array for the results.  These tests call it
-through the C ABI twice in a row with different tables and compare each result
-with the regular zmc_integrate entry point, within the tolerances the parity
-tests use (tests/gpu_common.py).  The file sorts last so that a run stopping at
-the first failure has already run every other test.
+descriptor table and a device array for the results.  The test calls it through
+the C ABI twice in a row on one stream, without waiting in between (the second
+call rewrites the shared array behind the first call's queued kernels, which
+only stream order keeps apart), each call writing its own output.  Both results
+must equal the regular zmc_integrate entry point's bit for bit (same chunk
+length, same records, same fixed-order merge), and separately match the FP64
+oracle's own estimates within the parity tolerances (tests/gpu_common.py).
+The file sorts last so that a run stopping at the first failure has already run
+every other test.
 """
 import numpy as np
 import pytest
@@ -37,17 +41,23 @@ def test_noalloc_matches_integrate_two_calls_in_a_row():
     with zmc.Context(arena_bytes=256 << 20) as ctx:
         refs = [zmc.zmc_integrate(ctx.handle, t) for t in tables]
     stream = torch.cuda.Stream()
-    for t, ref in zip(tables, refs):
-        # the caller owns the output; fill it with garbage to see it overwritten
-        out = torch.full((len(t) * zmc.RESULT_DTYPE.itemsize,), 0xFF, dtype=torch.uint8,
-                         device="cuda")
+    # the caller owns the outputs; fill them with garbage to see them overwritten
+    outs = [torch.full((len(t) * zmc.RESULT_DTYPE.itemsize,), 0xFF, dtype=torch.uint8,
+                       device="cuda") for t in tables]
+    torch.cuda.synchronize()
+    for t, out in zip(tables, outs):
         st = zmc.zmc_integrate_noalloc(t, out.data_ptr(), stream.cuda_stream)
         assert st == zmc.ZMC_OK, zmc.zmc_last_error()
-        stream.synchronize()
+    stream.synchronize()
+    for t, out, ref in zip(tables, outs, refs):
         got = out.cpu().numpy().view(zmc.RESULT_DTYPE)
-        want, _ = oracle.integrate(t)  # supplies mean|f| for the tolerance scale
-        want["estimate"] = ref["estimate"]
-        want["stderr"] = ref["stderr"]
+        # the same computation as zmc_integrate: equal bit for bit
+        assert np.array_equal(got["estimate"], ref["estimate"])
+        assert np.array_equal(got["stderr"], ref["stderr"], equal_nan=True)
+        assert np.array_equal(got["n"], ref["n"])
+        assert np.array_equal(got["status"], ref["status"])
+        # and, independently, the FP64 oracle on the same Philox samples
+        want, _ = oracle.integrate(t)
         G.compare(t, got, want)
 
 
