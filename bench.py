@@ -47,7 +47,14 @@ WORKLOAD = "fig1-harmonics-100x1e6-x10-repeats"
 # the phase carry, |x|, 1/4 - |x|, the integer -> float conversion and its scaling
 # -> 5; t^2, the degree-4 polynomial in t^2 with the amplitude in its
 # coefficients (4) and the product with t -> 6; shifted sums -> 3.
-def harmonic_ops_per_sample(d: int) -> float:
+# Rows whose dimensions all advance the phase at the same rate (k_i (hi_i - lo_i)
+# equal, d >= 2) take the equal-rate form: the 23-bit integers are summed
+# (mask + add per coordinate -> 2 d) and the phase is one widening multiply-add
+# and one multiply-add (2); then |x|, 1/4 - |x|, the conversion and its scaling
+# (4).
+def harmonic_ops_per_sample(d: int, equal_rates: bool = False) -> float:
+    if equal_rates:
+        return 8 * d + 0.8 * d + 2 * d + 2 + 4 + 6 + 3
     return 8 * d + 0.8 * d + 4 * d + 5 + 6 + 3
 
 
@@ -56,15 +63,32 @@ def harmonic_ops_per_sample(d: int) -> float:
 # a widening 32 x 32 -> 64 multiply counts 2 (it takes the pipe twice as long as
 # a 32-bit one).  Philox: 16 widening multiplies per block once the products
 # shared by a chunk are formed once, d / 5 blocks per sample -> 6.4 d; the
-# fixed-point phase: one 32-bit multiply-add per coordinate -> d.
-def harmonic_heavy_ops_per_sample(d: int) -> float:
-    return 2 * 16 * d / 5 + d
+# fixed-point phase: one 32-bit multiply-add per coordinate -> d, or for the
+# equal-rate form one widening and one 32-bit multiply-add -> 3.
+def harmonic_heavy_ops_per_sample(d: int, equal_rates: bool = False) -> float:
+    return 2 * 16 * d / 5 + (3 if equal_rates else d)
+
+
+def equal_rate_rows(table) -> np.ndarray:
+    """Harmonic rows the library evaluates in the equal-rate form: d >= 2 and
+    k_i (hi_i - lo_i) identical in every dimension (exact equality implies the
+    library's test, equal rates after rounding to 2^-41 turn)."""
+    out = np.zeros(len(table), dtype=bool)
+    for i, row in enumerate(table):
+        d = int(row["dim"])
+        if int(row["family"]) != W.HARMONIC or d < 2:
+            continue
+        rate = row["p"][2:2 + d] * (row["hi"][:d] - row["lo"][:d])
+        out[i] = bool(np.all(rate == rate[0]))
+    return out
 
 
 def table_mean(table, fn) -> float:
-    """Sample-weighted mean of fn(dim) over a table's rows."""
+    """Sample-weighted mean of fn(dim, equal_rates) over a table's rows."""
     n = table["n_samples"].astype(np.float64)
-    return float(np.sum(n * np.array([fn(int(d)) for d in table["dim"]])) / np.sum(n))
+    eq = equal_rate_rows(table)
+    per = np.array([fn(int(d), bool(e)) for d, e in zip(table["dim"], eq)])
+    return float(np.sum(n * per) / np.sum(n))
 
 
 # Sources of the dominant kernel (zmc_batched_kernel<HARMONIC>).
@@ -460,6 +484,18 @@ def run_native(args, world, rank, local):
         assert np.all(out["status"] == 0)
         e2e_s = max_over_ranks(world, sum(e2e_t) / len(e2e_t))
 
+    # The same workload through the general harmonic form: the Fig. 1 wave
+    # vectors are isotropic on the unit cube, so every dimension advances the
+    # phase at the same rate and the library takes its cheaper equal-rate form;
+    # stretching k_4 by 1e-9 (a phase change below 1e-8 rad) makes the rates
+    # differ and shows what a general wave vector costs.
+    general = None
+    if rank == 0 and not args.skip_mixed:
+        gt = tab.copy()
+        gt["p"][:, 5] *= 1.0 + 1e-9
+        general = batched_and_plain(zmc, torch, ctx, gt, flush,
+                                    "fig1-harmonics-100x1e6-x10, k_4 x (1 + 1e-9)", 20, False)
+
     # the 10^4-integrand mix and the Eq. 2 abs-linear set (batched and plain),
     # rank 0 only
     mixed = eq2 = None
@@ -539,6 +575,8 @@ def run_native(args, world, rank, local):
         "fmaheavy_frac": sig(roofline["frac"], 3),
         "issue_frac": sig(roofline["issue_slots"]["frac"], 3),
     }
+    if general:
+        summary["fig1_general_phase_gsps"] = sig(general["batched_gsps"])
     for key, leg in (("mix1e4", mixed), ("eq2_abslin", eq2)):
         if leg:
             summary[key] = {"batched_gsps": sig(leg["batched_gsps"]),
@@ -559,7 +597,7 @@ def run_native(args, world, rank, local):
         "per_integrand_fp32": None if per_row_ms is None else {
             "value": n_samples / (per_row_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": per_row_ms,
             "form": "the batched FP32 kernels, one launch (graph) per integrand"},
-        "mixed": mixed, "eq2_abslin": eq2, "serving": serving,
+        "fig1_general_phase": general, "mixed": mixed, "eq2_abslin": eq2, "serving": serving,
         "wall_s_timed": wall,
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

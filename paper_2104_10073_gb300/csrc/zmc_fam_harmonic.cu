@@ -19,16 +19,45 @@ namespace {
 // R cos(2 pi x) = R sin(2 pi (1/4 - |x|)), evaluated as t Pr(t^2) with Pr = R P,
 // P the degree-4 polynomial of zmc_coeffs.h: the amplitude goes into the
 // coefficients once per chunk instead of into every sample.
+//
+// Variant G = 1 (rows whose dimensions all advance the phase at the same rate,
+// T_i = T, as in the paper's Fig. 1 set k = kappa (1, 1, 1, 1) on the unit cube):
+// the phase is P0 + T S with S = sum_i m_i < 2^26, formed in integers: T_lo S
+// plus the low word of P0 + 1/2 unit by one widening multiply-add, whose high
+// word (the carry into whole units) T_hi S + P0_hi adds by one 32-bit
+// multiply-add.  So the phase is P0 + T S rounded to the nearest unit of 2^-32
+// turn (error <= 1/2 unit, against up to ~D units for the general form), and
+// one multiply-add and one widening multiply-add replace D multiply-adds and D
+// FMAs.
+// How much of the FP32 work is issued as packed pairs (they run on the pipe that
+// also takes Philox's widening multiplies, so packing trades issue slots for
+// that pipe's time): 0 none, 1 the low-word FMAs, 2 also the sine, 3 also the
+// sums (run_chunk).
+#ifndef ZMC_HARMONIC_PACK
+#define ZMC_HARMONIC_PACK 3
+#endif
+// 1: |x| of the phase by one abs.s32 instead of the sign-mask form.
+#ifndef ZMC_HARMONIC_IABS
+#define ZMC_HARMONIC_IABS 0
+#endif
+
 template <int D, int G>
 struct Eval<ZMC_HARMONIC, D, G> {
+  static constexpr bool kPackedSums = ZMC_HARMONIC_PACK >= 3;
   static constexpr int kPairs = D / 2;  // coordinate pairs (2i, 2i + 1) of the low-word FMAs
   uint32_t thi[D];
   float2 tlo2[kPairs + 1], kc2[kPairs + 1];  // (tlo, kc) of coordinates 2i, 2i + 1
-  uint32_t p0;
+  uint32_t p0, p0lo;
   float rc[5];  // R times the coefficients of P
   __device__ __forceinline__ void load(const FnDev *fn) {
+    if (G == 1) {  // T_hi at w[0], T_lo (u32) at w[1], the low word of P0 at w[2]
+      thi[0] = fn->w[0];
+      thi[1] = fn->w[1];
+      p0lo = fn->w[2];
+    } else {
 #pragma unroll
-    for (int i = 0; i < D; ++i) thi[i] = fn->w[i];
+      for (int i = 0; i < D; ++i) thi[i] = fn->w[i];
+    }
 #pragma unroll
     for (int i = 0; i < D; i += 2) {
       tlo2[i / 2] = make_float2(__uint_as_float(fn->w[7 + i]),
@@ -47,6 +76,20 @@ struct Eval<ZMC_HARMONIC, D, G> {
   // The phase of one sample as the integer y = 2^32 (1/4 - |x|), x the phase in
   // turns reduced to [-1/2, 1/2).  The low-word FMAs of coordinates 2i and 2i + 1
   // run as one packed pair (each half rounded as the scalar FMA).
+  // y = 2^32 (1/4 - |x|) of one sample (see fold), as a float.
+  __device__ __forceinline__ float phase_y(const uint32_t *r) const {
+    if (G == 1) {
+      uint32_t sm = 0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) sm += r[i] & 0x7FFFFFu;
+      // T_lo S + (P0 + 1/2 unit) in 64 bits (units of 2^-64 turn); its high
+      // word carries the rounded whole units
+      const uint64_t lo = static_cast<uint64_t>(thi[1]) * sm +
+                          ((static_cast<uint64_t>(p0) << 32) | p0lo);
+      return __int2float_rn(fold(thi[0] * sm + static_cast<uint32_t>(lo >> 32)));
+    }
+    return __int2float_rn(phase(r));
+  }
   __device__ __forceinline__ int32_t phase(const uint32_t *r) const {
     uint32_t acc = p0, lows = 0;
     uint32_t vb[D];
@@ -57,7 +100,7 @@ struct Eval<ZMC_HARMONIC, D, G> {
     }
 #pragma unroll
     for (int i = 0; i + 1 < D; i += 2) {
-#if ZMC_PACKED_F32
+#if ZMC_PACKED_F32 && ZMC_HARMONIC_PACK >= 1
       const float2 c = __ffma2_rn(
           tlo2[i / 2], make_float2(__uint_as_float(vb[i]), __uint_as_float(vb[i + 1])),
           kc2[i / 2]);
@@ -69,29 +112,38 @@ struct Eval<ZMC_HARMONIC, D, G> {
     }
     if (D & 1)  // the host folds the 0x4B000000 offsets into p0
       lows += __float_as_uint(fmaf(tlo2[kPairs].x, __uint_as_float(vb[D - 1]), kc2[kPairs].x));
-    acc += lows;
+    return fold(acc + lows);
+  }
+  // x = acc / 2^32 in [-1/2, 1/2) turn  ->  y = 2^32 (1/4 - |x|)
+  __device__ __forceinline__ static int32_t fold(uint32_t acc) {
     // x = acc / 2^32 in [-1/2, 1/2) turn; cos(2 pi x) = sin(2 pi y) with
     // y = 1/4 - |x| in [-1/4, 1/4], formed exactly in the integer (two's-complement
     // wrap makes x = -1/2 come out right) and converted with full relative
     // precision, so the value keeps its relative accuracy near the zeros.
+#if ZMC_HARMONIC_IABS
+    uint32_t ax;  // abs.s32 maps -2^31 to itself, as the wrap below needs
+    asm("abs.s32 %0, %1;" : "=r"(ax) : "r"(acc));
+#else
     const uint32_t sgn = static_cast<uint32_t>(static_cast<int32_t>(acc) >> 31);
     const uint32_t ax = (acc ^ sgn) - sgn;
+#endif
     return static_cast<int32_t>(0x40000000u - ax);
   }
-  __device__ __forceinline__ float operator()(const uint32_t *r) const {
-    const float t = __int2float_rn(phase(r)) * 0x1p-32f;
+  // R sin(2 pi t), t = y / 2^32, by the odd polynomial t (R P)(t^2).
+  __device__ __forceinline__ float sine(float y) const {
+    const float t = y * 0x1p-32f;
     const float z = t * t;
     float p = fmaf(rc[4], z, rc[3]);
     p = fmaf(p, z, rc[2]);
     p = fmaf(p, z, rc[1]);
     p = fmaf(p, z, rc[0]);
-    return __fmul_rn(t, p);  // never contracted with the sums' f - K
+    return __fmul_rn(t, p);
   }
-  // R sin(2 pi y) of two samples as packed pairs: the same operations as
+  __device__ __forceinline__ float operator()(const uint32_t *r) const { return sine(phase_y(r)); }
+  // R sin(2 pi t) of two samples as packed pairs: the same operations as
   // operator(), so the same values bit for bit.
-  __device__ __forceinline__ float2 sine2(int32_t ya, int32_t yb) const {
-    const float2 sc = make_float2(0x1p-32f, 0x1p-32f);
-    const float2 t = __fmul2_rn(make_float2(__int2float_rn(ya), __int2float_rn(yb)), sc);
+  __device__ __forceinline__ float2 sine2(float ya, float yb) const {
+    const float2 t = __fmul2_rn(make_float2(ya, yb), make_float2(0x1p-32f, 0x1p-32f));
     const float2 z = __fmul2_rn(t, t);
     float2 p = __ffma2_rn(make_float2(rc[4], rc[4]), z, make_float2(rc[3], rc[3]));
     p = __ffma2_rn(p, z, make_float2(rc[2], rc[2]));
@@ -100,21 +152,20 @@ struct Eval<ZMC_HARMONIC, D, G> {
     return __fmul2_rn(t, p);
   }
   __device__ __forceinline__ void quint(const uint32_t (&r)[5 * D], float (&f)[5]) const {
-    int32_t y[5];
+    float y[5];
 #pragma unroll
-    for (int t = 0; t < 5; ++t) y[t] = phase(r + t * D);
+    for (int t = 0; t < 5; ++t) y[t] = phase_y(r + t * D);
+#if ZMC_HARMONIC_PACK < 2
+#pragma unroll
+    for (int t = 0; t < 5; ++t) f[t] = sine(y[t]);
+    return;
+#endif
     const float2 a = sine2(y[0], y[1]), b = sine2(y[2], y[3]);
     f[0] = a.x;
     f[1] = a.y;
     f[2] = b.x;
     f[3] = b.y;
-    const float t4 = __int2float_rn(y[4]) * 0x1p-32f;
-    const float z4 = t4 * t4;
-    float p4 = fmaf(rc[4], z4, rc[3]);
-    p4 = fmaf(p4, z4, rc[2]);
-    p4 = fmaf(p4, z4, rc[1]);
-    p4 = fmaf(p4, z4, rc[0]);
-    f[4] = __fmul_rn(t4, p4);
+    f[4] = sine(y[4]);
   }
 };
 
@@ -123,6 +174,7 @@ __device__ void dispatch_item<ZMC_HARMONIC>(const FnDev *fn, uint64_t chunk, uin
                                       uint32_t lane) {
   switch (fn->variant) {
     ZMC_HARMONIC_VARIANTS(ZMC_ITEM_CASE)
+    ZMC_HARMONIC_EQUAL_VARIANTS(ZMC_ITEM_CASE)
     default:
       break;
   }
@@ -133,6 +185,7 @@ __device__ void dispatch_eval<ZMC_HARMONIC>(const FnDev *fn, uint64_t s_begin, u
                                       float *out) {
   switch (fn->variant) {
     ZMC_HARMONIC_VARIANTS(ZMC_EVAL_CASE)
+    ZMC_HARMONIC_EQUAL_VARIANTS(ZMC_EVAL_CASE)
     default:
       break;
   }

@@ -55,7 +55,9 @@ __host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t di
 //             unit of m_i, in units of 2^-64 turn): high word at w[i] (u32),
 //             fl32(low word / 2^32) at w[7+i], fl32(2^23 - w[7+i] 2^23) at w[14+i];
 //             P0 (u32, units of 2^-32 turn, minus the folded 2^23 offsets) w[21];
-//             S R at w[22].
+//             S R at w[22].  Variant degree 1 (D >= 2, every T_i equal to T): T's
+//             high word at w[0], its low word (u32) at w[1], P0 + 2^-33 turn to
+//             2^-64 turn (no offsets): high word w[21], low word w[2].
 //   ABSLIN    s = c.x in units of 2^-F (F per integrand, host-chosen):
 //             s 2^F = G0 + sum_i G_i vb_i + L, vb_i = 0x4B000000 + m_i, exact in
 //             64-bit integers (modulo 2^64) plus L = l0 + sum_i g_i fl(2^23 + m_i)

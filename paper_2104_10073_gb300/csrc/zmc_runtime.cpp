@@ -266,11 +266,15 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
       // in turns; k.x/(2 pi) = k.lo/(2 pi) + sum_i [k_i w_i / (2 pi)] m_i 2^-23.
       double phi = -std::atan2(p[1], p[0]) / kTwoPi;
       uint32_t fold = 0;  // the 2^23 offsets the kernel adds, removed from P0
+      uint64_t T0 = 0;
+      bool equal_rates = dim >= 2;  // every T_i the same: variant G = 1
       for (int i = 0; i < dim; ++i) {
         const double tau = p[2 + i] * w[i] / kTwoPi;
         if (!(std::fabs(tau) <= 1048576.0))
           return set_error(ZMC_EINVAL, "harmonic |k_i (hi_i-lo_i)| / 2pi above 2^20 turns");
         const uint64_t T = static_cast<uint64_t>(std::llround(std::ldexp(tau, 41)));
+        if (i == 0) T0 = T;
+        equal_rates = equal_rates && T == T0;
         const uint32_t thi = static_cast<uint32_t>(T >> 32);
         const double tlo = std::ldexp(static_cast<double>(static_cast<uint32_t>(T)), -32);
         const float tlo_f = static_cast<float>(tlo);
@@ -283,8 +287,19 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
       }
       if (!(std::fabs(phi) < 4.0e15)) return set_error(ZMC_EINVAL, "harmonic phase too large");
       const double fr = phi - std::floor(phi);  // exact, in [0, 1)
-      const uint32_t p0 = static_cast<uint32_t>(static_cast<uint64_t>(std::ldexp(fr, 64)) >> 32);
+      const uint64_t p0_64 = static_cast<uint64_t>(std::ldexp(fr, 64));  // exact
+      const uint32_t p0 = static_cast<uint32_t>((p0_64 + 0x80000000ull) >> 32);  // nearest
       fn->w[21] = p0 - fold;
+      if (equal_rates) {
+        // phase = P0 + T S (units of 2^-64 turn), S = sum_i m_i (no offsets),
+        // plus half a unit of 2^-32 turn so that the kernel's carry rounds it
+        const uint64_t p0r = p0_64 + 0x80000000ull;  // modulo one turn
+        fn->variant = variant_code(ZMC_HARMONIC, d.dim, 1);
+        fn->w[0] = static_cast<uint32_t>(T0 >> 32);
+        fn->w[1] = static_cast<uint32_t>(T0);
+        fn->w[2] = static_cast<uint32_t>(p0r);
+        fn->w[21] = static_cast<uint32_t>(p0r >> 32);
+      }
       const double R = S * std::hypot(p[0], p[1]);
       ok = finite_f32(R);
       put_f32(&fn->w[22], R);

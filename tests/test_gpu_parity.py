@@ -152,6 +152,50 @@ def test_single_sample_rows_keep_relative_accuracy(zctx, fam):
     G.compare(t, got, want)
 
 
+def _equal_rate_harmonics(n_rows, rng, n_lo, n_hi):
+    """Harmonic rows whose dimensions all advance the phase at the same rate
+    (k_i (hi_i - lo_i) equal: a scalar wave number on a cube of any offset), the
+    form the library evaluates through the phase of the coordinate sum: wave
+    numbers of either sign up to the validation limit's neighbourhood,
+    dimensions 2..7."""
+    t = W.empty(n_rows)
+    for i in range(n_rows):
+        d = int(rng.integers(2, 8))
+        width = float(rng.uniform(0.25, 2.0))
+        lo = float(rng.uniform(-3.0, 1.0))
+        kappa = float(rng.choice([-1.0, 1.0]) * 10 ** rng.uniform(-1.0, 3.0))
+        n = int(rng.integers(n_lo, n_hi + 1))
+        W.harmonic(t[i], float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2)), [kappa] * d,
+                   [lo] * d, [lo + width] * d, n, seed=int(rng.integers(0, 2**40)), stream_id=i)
+    return t
+
+
+def test_equal_rate_harmonics_per_sample(zctx):
+    """Per-sample values of the equal-rate form against the oracle's FP64 cos."""
+    t = _equal_rate_harmonics(40, np.random.default_rng(911), 10**6, 10**6)
+    for row in t:
+        for s0 in (0, 3, 500_000):
+            got = zmc.zmc_eval_samples(zctx.handle, row, s0, 501).astype(np.float64)
+            _, _, want = oracle.samples(row, s0, 501)
+            err = np.max(np.abs(got - want))
+            assert err <= 4e-6 * G.sample_scale(row), (int(row["dim"]), s0, err)
+
+
+def test_equal_rate_harmonics_single_samples_and_edges(zctx):
+    """Single-sample rows (relative accuracy next to zeros of cos) and sizes
+    around the quint and chunk boundaries, against the oracle."""
+    rng = np.random.default_rng(912)
+    ones = _equal_rate_harmonics(1500, rng, 1, 1)
+    got = zmc.zmc_integrate(zctx.handle, ones)
+    want, _ = oracle.integrate(ones)
+    G.compare(ones, got, want)
+    edges = _equal_rate_harmonics(len(EDGE_SIZES), rng, 1, 1)
+    edges["n_samples"] = EDGE_SIZES
+    got = zmc.zmc_integrate(zctx.handle, edges)
+    want, _ = oracle.integrate(edges)
+    G.compare(edges, got, want)
+
+
 def _abslin_scale_rows():
     """Abs-linear rows whose fixed-point scale 2^-F lands far from the usual:
     tiny, huge and mixed coefficient magnitudes, zero coefficients, boxes far
