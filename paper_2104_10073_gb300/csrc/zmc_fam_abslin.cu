@@ -13,6 +13,9 @@ namespace {
 // is harmless because the true sum fits, and the sub-unit remainders g_i m_i in
 // FP32 (error a few units).  One rounding to FP32 at the end keeps the relative
 // accuracy of f down to |c.x| of a few 2^-F.
+// Variant G = 1 (rows of many samples): the integer parts summed in 32 bits
+// (modulo 2^32; the host's scale keeps the true sum below 2^30), one 32-bit
+// multiply-add per coordinate.
 template <int D, int G>
 struct Eval<ZMC_ABSLIN, D, G> {
   int32_t gi[D];
@@ -30,6 +33,18 @@ struct Eval<ZMC_ABSLIN, D, G> {
     scale = __uint_as_float(fn->w[17]);
   }
   __device__ __forceinline__ float operator()(const uint32_t *r) const {
+    if (G == 1) {
+      uint32_t acc = static_cast<uint32_t>(g0);
+      float l = l0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const uint32_t vb = (r[i] & 0x7FFFFFu) | 0x4B000000u;  // bits of 2^23 + m_i
+        acc = static_cast<uint32_t>(gi[i]) * vb + acc;
+        l = fmaf(gl[i], __uint_as_float(vb), l);
+      }
+      const float s = __fadd_rn(__int2float_rn(static_cast<int32_t>(acc)), l);
+      return __fmul_rn(scale, fabsf(s));
+    }
     uint64_t acc = g0;
     float l = l0;
 #pragma unroll
@@ -49,6 +64,7 @@ __device__ void dispatch_item<ZMC_ABSLIN>(const FnDev *fn, uint64_t chunk, uint3
                                       uint32_t lane) {
   switch (fn->variant) {
     ZMC_ABSLIN_VARIANTS(ZMC_ITEM_CASE)
+    ZMC_VARIANTS_DIM(ZMC_ITEM_CASE, ZMC_ABSLIN, 1)
     default:
       break;
   }
@@ -59,6 +75,7 @@ __device__ void dispatch_eval<ZMC_ABSLIN>(const FnDev *fn, uint64_t s_begin, uin
                                       float *out) {
   switch (fn->variant) {
     ZMC_ABSLIN_VARIANTS(ZMC_EVAL_CASE)
+    ZMC_VARIANTS_DIM(ZMC_EVAL_CASE, ZMC_ABSLIN, 1)
     default:
       break;
   }

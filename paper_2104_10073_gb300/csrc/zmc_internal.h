@@ -63,6 +63,8 @@ __host__ __device__ constexpr uint32_t variant_code(uint32_t family, uint32_t di
 //             64-bit integers (modulo 2^64) plus L = l0 + sum_i g_i fl(2^23 + m_i)
 //             in FP32: G_i (s32) at w[i], g_i (FP32, |g_i| <= 1/2) at w[7+i],
 //             G0 (u64) at w[14] (lo), w[15] (hi), l0 at w[16], S a 2^-F at w[17].
+//             Variant degree 1 (rows of >= 256 samples): the same with F such that
+//             |c.x| 2^F <= 2^29 on the box, the integer sum taken modulo 2^32.
 //   GAUSS     t_i = (x_i - mu_i) beta, beta = sqrt(log2(e) / 2) / sigma, so that
 //             f = A 2^(-sum t_i^2);  h_i = (hi_i - lo_i) beta: hi w[i], lo w[7+i];
 //             S A w[28].  Variant degree 0 ("near": mu_i / box position within

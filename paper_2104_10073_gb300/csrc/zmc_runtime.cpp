@@ -188,6 +188,9 @@ static bool poly_roots_payload(const double (*e)[5], int dim, int g, double S, F
   return true;
 }
 
+// Abs-linear rows with at least this many samples use the 32-bit sum of c.x.
+constexpr uint64_t kAbsLinNarrowMinSamples = 256;
+
 zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volume) {
   if (d.family > ZMC_POLY) return set_error(ZMC_EINVAL, "unknown family %u", d.family);
   if (d.dim < 1 || d.dim > kMaxDim) return set_error(ZMC_EINVAL, "dim %u not in 1..7", d.dim);
@@ -312,17 +315,34 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
       // and the remainders g_i = T_i 2^F - G_i (|g_i| <= 1/2) in FP32.  It multiplies
       // G_i by vb_i = 0x4B000000 + m_i, whose bits are also the float 2^23 + m_i,
       // so the offsets G_i 0x4B000000 and 2^23 g_i are taken out of the constants.
-      double s0 = 0.0, tmax = 0.0, smax = 0.0;
+      //
+      // Rows of at least kAbsLinNarrowMinSamples samples (variant degree 1) take a
+      // 32-bit integer sum instead: units of 2^-F with |c.x| 2^F <= 2^29 over the
+      // box, one 32-bit multiply-add per coordinate.  Its error, a few units of
+      // the FP32 remainder sum (<= D^2 / 4), stays below ~2e-8 of max|c.x|, i.e.
+      // below 2e-7 of mean|c.x| (at least a tenth of the maximum for a box of up
+      // to 7 dimensions): far inside 1e-6 of the estimate's mean|f| once the row
+      // has enough samples for its sample mean of |f| to be near the true one.
+      // Rows with fewer samples, down to a single one next to the hyperplane,
+      // keep the 64-bit sum.
+      double s0 = 0.0, tmax = 0.0, smax = 0.0, up = 0.0, dn = 0.0;
       for (int i = 0; i < dim; ++i) {
-        s0 += p[1 + i] * d.lo[i];
-        tmax = std::max(tmax, std::fabs(p[1 + i] * w[i]) * 0x1p-23);
-        smax += std::fabs(p[1 + i]) * std::max(std::fabs(d.lo[i]), std::fabs(d.hi[i]));
+        const double c = p[1 + i];
+        s0 += c * d.lo[i];
+        tmax = std::max(tmax, std::fabs(c * w[i]) * 0x1p-23);
+        smax += std::fabs(c) * std::max(std::fabs(d.lo[i]), std::fabs(d.hi[i]));
+        up += c * (c > 0 ? d.hi[i] : d.lo[i]);
+        dn += c * (c > 0 ? d.lo[i] : d.hi[i]);
       }
       if (!std::isfinite(s0) || !std::isfinite(smax) || !std::isfinite(tmax))
         return set_error(ZMC_EINVAL, "abs-linear constants not finite");
+      const bool narrow = d.n_samples >= kAbsLinNarrowMinSamples;
+      const double srange = std::max(std::fabs(up), std::fabs(dn));  // max |c.x| on the box
       int F = 1000;
       if (tmax > 0.0) F = std::min(F, static_cast<int>(std::floor(std::log2(2147483647.0 / tmax))));
-      if (smax > 0.0) F = std::min(F, 61 - static_cast<int>(std::ceil(std::log2(smax))));
+      if (narrow && srange > 0.0)
+        F = std::min(F, 29 - static_cast<int>(std::ceil(std::log2(srange))));
+      if (!narrow && smax > 0.0) F = std::min(F, 61 - static_cast<int>(std::ceil(std::log2(smax))));
       if (F == 1000) F = 0;
       F = std::max(-900, F);
       // log2 rounding can overshoot by one at a power of two: step down until
@@ -345,6 +365,7 @@ zmc_status precompute(const zmc_desc &d, FnDev *fn, PlainFn *plain, double *volu
       fn->w[14] = static_cast<uint32_t>(g0);
       fn->w[15] = static_cast<uint32_t>(g0 >> 32);
       std::memcpy(&fn->w[16], &l0, 4);
+      if (narrow) fn->variant = variant_code(ZMC_ABSLIN, d.dim, 1);
       const double sc = S * p[0] * std::ldexp(1.0, -F);
       ok = finite_f32(sc) && (sc == 0.0 || std::fabs(sc) >= 0x1p-126);
       put_f32(&fn->w[17], sc);

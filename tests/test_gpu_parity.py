@@ -222,6 +222,34 @@ def _abslin_scale_rows():
     return tab
 
 
+def test_abslin_32bit_sum_rows(zctx):
+    """Rows of >= 256 samples take the 32-bit sum of c.x: sizes around that
+    threshold, every dimension, against the oracle.  Boxes: centred on the
+    hyperplane (mean|f| smallest against max|f|), far from the origin with
+    alternating coefficient signs (terms of 1e3 cancelling to c.x of order 1),
+    tiny and huge coefficients, random coefficient signs."""
+    rng = np.random.default_rng(4321)
+    rows = []
+    for d in range(1, 8):
+        alt = [1.0 if i % 2 == 0 else -1.0 for i in range(d)]
+        for n in (255, 256, 257, 1000, 4161):
+            rnd = list(rng.choice([-1.0, 1.0], size=d))
+            for c, lo, hi in ((rnd, [-0.5] * d, [0.5] * d),
+                              (alt, [1e3] * d, [1e3 + 1.0] * d),
+                              ([1e-12 * x for x in rnd], [-2.0] * d, [1.5] * d),
+                              ([1e9 * x for x in alt], [-1.0] * d, [1.0] * d)):
+                t = W.empty(1)
+                W.abslin(t[0], float(rng.uniform(0.5, 2.0)), c, lo, hi, n, seed=n + d,
+                         stream_id=len(rows))
+                rows.append(t[0])
+    tab = W.empty(len(rows))
+    for i, r in enumerate(rows):
+        tab[i] = r
+    got = zmc.zmc_integrate(zctx.handle, tab)
+    want, _ = oracle.integrate(tab)
+    G.compare(tab, got, want)
+
+
 def test_abslin_fixed_point_scale_edge_cases(zctx):
     t = _abslin_scale_rows()
     got = zmc.zmc_integrate(zctx.handle, t)
