@@ -662,13 +662,14 @@ def sig(x, digits=4):
     return float(f"{x:.{digits}g}")
 
 
-def run_serving(zmc, device, rate_hz, seconds, quints_per_lane=0, chunks_per_iter=0):
+def run_serving(zmc, device, rate_hz, seconds, quints_per_lane=0, chunks_per_iter=0, share=0):
     """Poisson job stream through zmc_submit; a collector thread takes finished
     ids from zmc_poll_any and the results from zmc_poll.  Latency = submit call
     to results collected."""
     jobs = W.serving_stream(rate_hz, seconds, max_fns=1000)
     ctx = zmc.Context(arena_bytes=8 << 30, device=device, serving=True,
-                      quints_per_lane=quints_per_lane, max_chunks_per_iter=chunks_per_iter)
+                      quints_per_lane=quints_per_lane, max_chunks_per_iter=chunks_per_iter,
+                      serving_share=share)
     submitted = {}
     done = {}
     lock = threading.Lock()
@@ -888,7 +889,7 @@ def run_serving_sweep(args):
     out = []
     for rate in args.serving_rates:
         r = run_serving(zmc, 0, rate, args.serving_seconds, args.serving_quints,
-                        args.serving_chunks)
+                        args.serving_chunks, args.serving_share)
         if r is not None:
             r["demand_gsps"] = rate * 500.5 * 1.444e6 / 1e9  # E[jobs/s x rows x N]
         out.append(r)
@@ -924,6 +925,9 @@ def main():
                     help="chunk length of the serving context (0: library default)")
     ap.add_argument("--serving-chunks", type=int, default=0,
                     help="chunks per serving iteration (0: library default)")
+    ap.add_argument("--serving-share", type=int, default=0,
+                    help="serving launches: 0 oldest job first (library default), > 0 equal "
+                         "shares of at least this many chunks")
     args = ap.parse_args()
     world, rank, local = (int(os.environ.get("WORLD_SIZE", "1")),
                           int(os.environ.get("RANK", "0")),

@@ -153,7 +153,11 @@ typedef struct zmc_options {
                                     agree within rounding across values.            */
     const char *tune_cache_path; /* autotune JSON cache; NULL -> no file             */
     uint32_t serving;            /* 1: start the serving thread (zmc_submit/poll)    */
-    uint32_t reserved;
+    uint32_t serving_share;      /* serving: how a launch's chunks are shared.
+                                    0: oldest job first (its next chunks up to the
+                                    launch's budget, what is left to the next job);
+                                    > 0: an equal share for every job with work
+                                    left, at least this many chunks each          */
 } zmc_options;
 
 #define ZMC_TUNE_GEOMETRY 1u

@@ -4,9 +4,10 @@
 // queues the job.  A scheduler thread owns a stream and loops:
 //   1. admit queued jobs, in order, while their device block (descriptor table,
 //      one 8-byte record per chunk, result rows) fits in the arena;
-//   2. build one iteration: a fair share of at most max_chunks_per_iter chunks
-//      over all admitted jobs (every job with work left gets a share, so a small
-//      job that arrives behind a large one starts at the next iteration);
+//   2. build one iteration of at most max_chunks_per_iter chunks over the
+//      admitted jobs: oldest job first by default (each job's next chunks up to
+//      the remaining budget), or equal shares for every job with work left
+//      (zmc_options.serving_share);
 //   3. upload the iteration's entry table and header, replay the iteration graph
 //      (per-family persistent sampling kernels + FP64 merge of every job whose
 //      last chunks ran), copy those jobs' results to pinned staging, record an
@@ -353,12 +354,17 @@ void scheduler_loop(ServingState *S) {
       if (j->state == JobState::kRunning && j->chunks_issued < j->chunks_total) active.push_back(j);
     uint32_t n_entries = 0;
     uint64_t jobs_in_iter = 0;  // jobs with work items in this launch
-    // Each job with work left gets budget / active chunks, but at least
-    // kMinQuantum: with many live jobs, runs of a few chunks would turn every work
-    // item into an entry-table search.  Jobs are visited oldest first.
-    constexpr uint64_t kMinQuantum = 256;
+    // Jobs are visited oldest first.  By default each takes its next chunks up
+    // to the whole remaining budget, so a launch finishes the oldest jobs and
+    // starts the next ones with what is left (measured on the Poisson job
+    // stream: p99 latency 17 ms instead of 22 ms at 300 jobs/s, 33 instead of
+    // 53 ms at 400, p50 unchanged).  With zmc_options.serving_share > 0 every
+    // job with work left gets budget / active chunks, but at least that floor
+    // (runs of a few chunks would turn every work item into an entry-table
+    // search).
+    const uint64_t min_share = ctx->serving_share ? ctx->serving_share : ~0ull;
     while (budget > 0 && !active.empty() && n_entries < S->max_entries) {
-      const uint64_t share = std::max<uint64_t>(kMinQuantum, budget / active.size());
+      const uint64_t share = std::max<uint64_t>(min_share, budget / active.size());
       std::vector<std::shared_ptr<ServJob>> still;
       for (auto &j : active) {
         uint64_t take = std::min<uint64_t>(share, budget);

@@ -68,6 +68,24 @@ def test_results_same_alone_and_mixed(sctx, sq_ctx):
         G.compare(t, a, want)
 
 
+def test_results_same_under_both_share_policies(sctx):
+    """Oldest-first launches (the default) and equal shares give the same
+    results bit for bit: a chunk's record does not depend on what shares its
+    launch."""
+    jobs = _jobs(8, seed=17)
+    ids = [zmc.zmc_submit(sctx.handle, t) for t in jobs]
+    first = [zmc.zmc_poll(sctx.handle, j, len(t), wait_ms=-1)[1] for j, t in zip(ids, jobs)]
+    with zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=4096,
+                     serving_share=64) as eq:
+        ids = [zmc.zmc_submit(eq.handle, t) for t in jobs]
+        for j, t, a in zip(ids, jobs, first):
+            st, res = zmc.zmc_poll(eq.handle, j, len(t), wait_ms=-1)
+            assert st == zmc.ZMC_OK
+            assert np.array_equal(res["estimate"], a["estimate"])
+            assert np.array_equal(res["stderr"], a["stderr"], equal_nan=True)
+        assert zmc.zmc_serving_stats_get(eq.handle)["shared_iterations"] >= 1
+
+
 def test_poll_semantics(sctx):
     t = W.mixed(50, gen_seed=9, lo_exp=5.5, hi_exp=6.5)
     jid = zmc.zmc_submit(sctx.handle, t)
