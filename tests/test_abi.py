@@ -90,14 +90,18 @@ def test_validation_family_specific(lib):
 
 
 def test_validation_accepts_abslin_at_any_scale(lib):
-    """The exact abs-linear sum picks its fixed-point scale per integrand; tiny,
-    huge and mixed coefficient magnitudes and zero coefficients are all valid."""
-    for c in ([1e-20, -2e-20], [3e15, -1e15, 2e15], [1e8, 1e-8], [0.0, 1.0, 0.0], [0.0, 0.0],
-              [1e-300, 1.0], [1e30, -1e30]):
-        t = W.empty(1)
-        W.abslin(t[0], 1.0, c, [-1.0] * len(c), [1.0] * len(c), 10)
-        st, bad, msg = zmc.zmc_validate(t)
-        assert st == zmc.ZMC_OK, (c, msg)
+    """The abs-linear sum picks its fixed-point scale per integrand, for the
+    64-bit sum (rows of < 256 samples) and the 32-bit one (>= 256); tiny, huge
+    and mixed coefficient magnitudes, zero coefficients and boxes far from the
+    origin are all valid for both."""
+    for n in (10, 256, 10**6):
+        for c in ([1e-20, -2e-20], [3e15, -1e15, 2e15], [1e8, 1e-8], [0.0, 1.0, 0.0],
+                  [0.0, 0.0], [1e-300, 1.0], [1e30, -1e30]):
+            for lo, hi in ((-1.0, 1.0), (1e6, 1e6 + 1.0)):
+                t = W.empty(1)
+                W.abslin(t[0], 1.0, c, [lo] * len(c), [hi] * len(c), n)
+                st, bad, msg = zmc.zmc_validate(t)
+                assert st == zmc.ZMC_OK, (n, c, lo, msg)
 
 
 def test_validation_of_an_empty_table(lib):
