@@ -568,9 +568,7 @@ zmc_status check_ctx(zmc_ctx *ctx) {
 zmc_status plan_autotune(zmc_plan *plan) {
   zmc_ctx *ctx = plan->ctx;
   cudaStream_t str = ctx->stream;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  ZMC_CUDA(ctx, cudaEventCreate(&e0));
-  ZMC_CUDA(ctx, cudaEventCreate(&e1));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;  // created at the first cache miss
   zmc_status st = ZMC_OK;
   for (int f = 0; f < 4 && st == ZMC_OK; ++f) {
     if (plan->fam_items[f] == 0) continue;
@@ -583,6 +581,14 @@ zmc_status plan_autotune(zmc_plan *plan) {
                                plan->fam_items[f], U);
       plan->tune_source[f] = 2;
       continue;
+    }
+    if (!e0) {
+      cudaError_t ce = cudaEventCreate(&e0);
+      if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+      if (ce != cudaSuccess) {
+        st = ctx_cuda_fail(ctx, ce, "autotune events");
+        break;
+      }
     }
     // a slice of about 32 items per resident warp at the largest geometry
     LaunchHdr th = plan->h_hdr;
@@ -625,9 +631,11 @@ zmc_status plan_autotune(zmc_plan *plan) {
     plan->tune_source[f] = 1;
     tune_cache_store(ctx, key, best);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  const bool timed = e0 != nullptr;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   if (st != ZMC_OK) return st;
+  if (!timed) return ZMC_OK;  // every family from the cache: nothing ran
   // put the real header back (the slices overwrote it)
   ZMC_CUDA(ctx, cudaMemcpyAsync(plan->d_hdr, &plan->h_hdr, sizeof plan->h_hdr,
                                 cudaMemcpyHostToDevice, str));
@@ -643,7 +651,7 @@ struct PlanChoice {
 
 zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out,
                       const uint64_t *s_begin = nullptr, const uint64_t *s_end = nullptr,
-                      const PlanChoice *force = nullptr);
+                      const PlanChoice *force = nullptr, bool wait_upload = true);
 void plan_free(zmc_plan *plan);
 
 // The key of a table's shape class for the chunk tuner: the GPU, the families
@@ -780,8 +788,12 @@ zmc_status choose_chunk(zmc_ctx *ctx, const zmc_desc *desc, size_t n, PlanChoice
 
 // ranges: optional [s_begin[i], s_end[i]) sample ranges (moments output).
 // force: a fixed chunk length and unroll, no autotuning (trial plans).
+// wait_upload = false: the caller's next use of the staging buffer is
+// stream-ordered after the upload (a device-to-host copy of results), so the
+// host need not wait for the upload here.
 zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **out,
-                      const uint64_t *s_begin, const uint64_t *s_end, const PlanChoice *force) {
+                      const uint64_t *s_begin, const uint64_t *s_end, const PlanChoice *force,
+                      bool wait_upload) {
   if (!desc || !out || n == 0) return set_error(ZMC_EINVAL, "need n >= 1 descriptors");
   if (n >= (1u << 31)) return set_error(ZMC_EINVAL, "too many descriptors");
   auto plan = std::make_unique<zmc_plan>();
@@ -923,6 +935,7 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
     return st;
   }
   // the staging buffer is reused by the next call, so the copies are waited for
+  // (unless the caller's next use of it is stream-ordered: wait_upload)
   char *s = static_cast<char *>(ctx->stage);
   std::memcpy(s, fns.data(), fn_bytes);
   std::memcpy(s + fn_bytes, ents.data(), ent_bytes);
@@ -938,7 +951,7 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(plan->d_hdr, s + fn_bytes + ent_bytes + mrg_bytes, sizeof h,
                         cudaMemcpyHostToDevice, str);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+  if (e == cudaSuccess && wait_upload) e = cudaStreamSynchronize(str);
   if (e != cudaSuccess) {
     plan->release_all();
     return ctx_cuda_fail(ctx, e, "plan upload");
@@ -1261,7 +1274,8 @@ zmc_status zmc_integrate(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_resul
   if (!out) return set_error(ZMC_EINVAL, "null output");
   std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
   zmc_plan *plan = nullptr;
-  st = plan_build(ctx, desc, n, &plan);
+  // the results copy below is the next use of the staging buffer, stream-ordered
+  st = plan_build(ctx, desc, n, &plan, nullptr, nullptr, nullptr, false);
   if (st != ZMC_OK) return st;
   st = plan_enqueue(plan, ZMC_STAGE_ALL);
   if (st == ZMC_OK) st = plan_results_to(plan, out);
@@ -1291,7 +1305,7 @@ zmc_status zmc_integrate_moments(zmc_ctx *ctx, const zmc_desc *desc, const uint6
   static_assert(sizeof(zmc_moments) == sizeof(zmc_result), "moments share the result slot");
   std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
   zmc_plan *plan = nullptr;
-  st = plan_build(ctx, desc, n, &plan, s_begin, s_end);
+  st = plan_build(ctx, desc, n, &plan, s_begin, s_end, nullptr, false);
   if (st != ZMC_OK) return st;
   st = plan_enqueue(plan, ZMC_STAGE_ALL);
   if (st == ZMC_OK) st = plan_results_to(plan, reinterpret_cast<zmc_result *>(out));
@@ -1328,7 +1342,7 @@ zmc_status zmc_integrate_functional(zmc_ctx *ctx, const zmc_desc *base, const ui
   }
   std::lock_guard<std::recursive_mutex> g(ctx->api_mu);
   zmc_plan *plan = nullptr;
-  st = plan_build(ctx, table.data(), n_points, &plan);
+  st = plan_build(ctx, table.data(), n_points, &plan, nullptr, nullptr, nullptr, false);
   if (st != ZMC_OK) return st;
   st = plan_enqueue(plan, ZMC_STAGE_ALL);
   if (st == ZMC_OK) st = plan_results_to(plan, out);
