@@ -704,12 +704,14 @@ zmc_status time_family(zmc_plan *plan, int f, int unroll, cudaEvent_t e0, cudaEv
   return ZMC_OK;
 }
 
-// Samples of the table subset the chunk tuner times each candidate on.
+// Samples and rows of the table subset the chunk tuner times each candidate on.
 constexpr double kTrialSamples = 2147483648.0;
+constexpr size_t kTrialRows = 1u << 16;
 
 // Chunk tuner: the chunk length (kTuneQuints) and per-family unroll under which
-// a bounded subset of the table's rows (every k-th row, whole rows) samples
-// fastest, or the cached choice for the table's shape class.  Each candidate
+// a bounded subset of the table's rows (every k-th row, whole rows; at most
+// ~2^31 samples and 2^16 rows) samples fastest, or the cached choice for the
+// table's shape class.  Each candidate
 // chunk length builds a trial plan of the subset; each family kernel present is
 // timed alone at both unrolls.  *source: 1 measured, 2 cached, 0 left at the
 // defaults (a trial plan did not fit the arena).
@@ -725,8 +727,9 @@ zmc_status choose_chunk(zmc_ctx *ctx, const zmc_desc *desc, size_t n, PlanChoice
   }
   double total = 0.0;
   for (size_t i = 0; i < n; ++i) total += static_cast<double>(desc[i].n_samples);
-  const size_t stride =
-      total <= kTrialSamples ? 1 : static_cast<size_t>(std::ceil(total / kTrialSamples));
+  const size_t stride = std::max<size_t>(
+      total <= kTrialSamples ? 1 : static_cast<size_t>(std::ceil(total / kTrialSamples)),
+      (n + kTrialRows - 1) / kTrialRows);
   std::vector<zmc_desc> sub;
   for (size_t i = 0; i < n; i += stride) sub.push_back(desc[i]);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
