@@ -402,79 +402,6 @@ __device__ __forceinline__ void run_chunk(const FnDev *__restrict__ fn, uint64_t
   if (lane == 0) fn->rec[chunk] = make_float2(mean, m2);
 }
 
-// Software-pipelined form of run_chunk's full-chunk path: each loop step
-// generates the Philox blocks of the lane's next quint while it evaluates and
-// sums the current one, so one warp's instruction stream mixes the generator's
-// widening multiplies with the evaluation's ALU and FP32 work.  The step after
-// the last quint generates one quint that is not used.  Same sums, same order
-// as run_chunk<..., true>.
-#ifndef ZMC_PIPELINE
-#define ZMC_PIPELINE 0
-#endif
-template <int FAM, int D, int G>
-__device__ __forceinline__ void run_chunk_pipelined(const FnDev *__restrict__ fn, uint64_t chunk,
-                                                    uint32_t Q, uint32_t lane) {
-  Eval<FAM, D, G> ev;
-  ev.load(fn);
-  const RoundKeys rk = make_round_keys(fn->key0, fn->key1);
-  const uint64_t quint0 = (fn->s_off + chunk * chunk_samples_of(Q)) / kQuint;
-  const uint64_t block0 = quint0 * D;
-  const uint32_t base_lo0 = static_cast<uint32_t>(block0) + lane * D;
-  const StreamPrefix sp =
-      make_stream_prefix(rk, fn->stream_id, static_cast<uint32_t>(block0 >> 32));
-  constexpr bool kPackedSums = ZMC_PACKED_F32 && PackedSums<Eval<FAM, D, G>>::value;
-  float n = 0.0f, mean = 0.0f, m2 = 0.0f;
-  uint32_t r[5 * D];
-  gen_quint_fast<D>(base_lo0, sp, r);
-  for (uint32_t jb = 0; jb < Q; jb += kBlockQuints) {
-    const uint32_t je = jb + kBlockQuints < Q ? jb + kBlockQuints : Q;
-    float K = 0.0f, s1 = 0.0f, s2 = 0.0f;
-    float2 s1p = make_float2(0.0f, 0.0f), s2p = make_float2(0.0f, 0.0f), nK2;
-#pragma unroll 2
-    for (uint32_t j = jb; j < je; ++j) {
-      uint32_t rn[5 * D];
-      gen_quint_fast<D>(base_lo0 + 32u * D * (j + 1), sp, rn);
-      float f[5];
-      eval_quint<D>(ev, r, f);
-      if (j == jb) {
-        K = f[0];
-        nK2 = make_float2(-K, -K);
-      }
-      if (kPackedSums) {
-        const float2 f01 = make_float2(f[0], f[1]), f23 = make_float2(f[2], f[3]);
-        s1p = __fadd2_rn(s1p, f01);
-        s1p = __fadd2_rn(s1p, f23);
-        s1 += f[4];
-        const float2 d01 = __fadd2_rn(f01, nK2), d23 = __fadd2_rn(f23, nK2);
-        s2p = __ffma2_rn(d01, d01, s2p);
-        s2p = __ffma2_rn(d23, d23, s2p);
-        const float d4 = f[4] - K;
-        s2 = fmaf(d4, d4, s2);
-      } else {
-        s1 += ((f[0] + f[1]) + (f[2] + f[3])) + f[4];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-          const float dlt = f[t] - K;
-          s2 = fmaf(dlt, dlt, s2);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 5 * D; ++k) r[k] = rn[k];
-    }
-    if (kPackedSums) {
-      s1 += s1p.x + s1p.y;
-      s2 += s2p.x + s2p.y;
-    }
-    const float nb = static_cast<float>(kQuint * (je - jb));
-    const float mb = __fdiv_rn(s1, nb);
-    const float dk = __fsub_rn(mb, K);
-    const float m2b = fmaxf(fmaf(__fmul_rn(-nb, dk), dk, s2), 0.0f);
-    chan_step(n, mean, m2, nb, mb, m2b);
-  }
-  warp_chan_merge(n, mean, m2);
-  if (lane == 0) fn->rec[chunk] = make_float2(mean, m2);
-}
-
 template <int FAM, int D, int G>
 __device__ __forceinline__ void run_item(const FnDev *__restrict__ fn, uint64_t chunk,
                                          uint32_t Q, uint32_t lane) {
@@ -483,12 +410,9 @@ __device__ __forceinline__ void run_item(const FnDev *__restrict__ fn, uint64_t 
   const bool full = fn->n_samples - s0 >= chunk_samples;
   const uint64_t b_first = ((fn->s_off + s0) / kQuint) * D;
   const uint64_t b_last = b_first + (chunk_samples / kQuint) * D - 1;
-  if (full && (b_first >> 32) == (b_last >> 32)) {
-    if (ZMC_PIPELINE && FAM == ZMC_HARMONIC)
-      run_chunk_pipelined<FAM, D, G>(fn, chunk, Q, lane);
-    else
-      run_chunk<FAM, D, G, true>(fn, chunk, Q, lane);
-  } else
+  if (full && (b_first >> 32) == (b_last >> 32))
+    run_chunk<FAM, D, G, true>(fn, chunk, Q, lane);
+  else
     run_chunk<FAM, D, G, false>(fn, chunk, Q, lane);
 }
 
