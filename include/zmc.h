@@ -510,6 +510,23 @@ zmc_status zmc_integrate_noalloc(const zmc_desc *desc, size_t n, zmc_result *out
  * the first rejected row. */
 zmc_status zmc_validate(const zmc_desc *desc, size_t n, size_t *bad_index);
 
+/* Host-only inspection (no GPU needed): the evaluation form the library picks
+ * for each of n descriptors, written to forms[i] as
+ *     (form << 8) | (family << 4) | dim,
+ * with form, by family:
+ *   ZMC_HARMONIC  0 general phase; 1 equal phase rates in every dimension
+ *                 (dim >= 2 and every k_i (hi_i - lo_i) the same after rounding
+ *                 to 2^-41 turn): the phase through the sum of the coordinates
+ *   ZMC_ABSLIN    0 c.x summed in 64-bit integers; 1 in 32-bit integers (rows of
+ *                 >= 256 samples)
+ *   ZMC_GAUSS     0 mu within [-1, 2] box widths of lo in every dimension; 1 not
+ *   ZMC_POLY      deg (0..4): coefficient form; deg + 3 (5..7): factors in
+ *                 root form (degrees 2..4)
+ * Rows the rules of zmc_desc reject give ZMC_EINVAL and *bad_index (if not
+ * NULL), as zmc_validate.  Forms never change what is integrated, only how
+ * (tests use this to check that their tables reach every form). */
+zmc_status zmc_variant_of(const zmc_desc *desc, size_t n, uint32_t *forms, size_t *bad_index);
+
 /* sizeof checks for foreign-language bindings. */
 size_t zmc_desc_size(void);
 size_t zmc_result_size(void);

@@ -1089,6 +1089,20 @@ zmc_status zmc_validate(const zmc_desc *desc, size_t n, size_t *bad_index) {
 }
 size_t zmc_result_size(void) { return sizeof(zmc_result); }
 
+zmc_status zmc_variant_of(const zmc_desc *desc, size_t n, uint32_t *forms, size_t *bad_index) {
+  if ((!desc || !forms) && n) return set_error(ZMC_EINVAL, "null argument");
+  for (size_t i = 0; i < n; ++i) {
+    FnDev fn;
+    const zmc_status st = precompute(desc[i], &fn, nullptr, nullptr);
+    if (st != ZMC_OK) {
+      if (bad_index) *bad_index = i;
+      return set_error(st, "descriptor %zu: %s", i, zmc_last_error(nullptr));
+    }
+    forms[i] = fn.variant;
+  }
+  return ZMC_OK;
+}
+
 zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   if (!out) return set_error(ZMC_EINVAL, "null output pointer");
   *out = nullptr;

@@ -118,6 +118,7 @@ _SIGS = {
     "zmc_philox_rate": ([_P, ctypes.c_uint64, _P], ctypes.c_int),
     "zmc_eval_samples": ([_P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_validate": ([_P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "zmc_variant_of": ([_P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "zmc_integrate_noalloc": ([_P, ctypes.c_size_t, _P, _P], ctypes.c_int),
     "zmc_udf_create": ([ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                         ctypes.POINTER(_P)], ctypes.c_int),
@@ -412,6 +413,21 @@ def zmc_validate(desc):
     if st == ZMC_OK:
         return st, None, ""
     return st, bad.value, zmc_last_error()
+
+
+def zmc_variant_of(desc) -> np.ndarray:
+    """The evaluation form the library picks per row (zmc_variant_of): a
+    structured array (family, dim, form); host only."""
+    t = _table(desc)
+    codes = np.zeros(len(t), dtype=np.uint32)
+    bad = ctypes.c_size_t(0)
+    _check(lib().zmc_variant_of(t.ctypes.data, len(t), codes.ctypes.data, ctypes.byref(bad)),
+           "zmc_variant_of")
+    out = np.zeros(len(t), dtype=[("family", "u4"), ("dim", "u4"), ("form", "u4")])
+    out["family"] = (codes >> 4) & 0xF
+    out["dim"] = codes & 0xF
+    out["form"] = codes >> 8
+    return out
 
 
 # ------------------------------------------------------------------ convenience

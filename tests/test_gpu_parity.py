@@ -173,6 +173,7 @@ def _equal_rate_harmonics(n_rows, rng, n_lo, n_hi):
 def test_equal_rate_harmonics_per_sample(zctx):
     """Per-sample values of the equal-rate form against the oracle's FP64 cos."""
     t = _equal_rate_harmonics(40, np.random.default_rng(911), 10**6, 10**6)
+    assert np.all(zmc.zmc_variant_of(t)["form"] == 1)  # the equal-rate form
     for row in t:
         for s0 in (0, 3, 500_000):
             got = zmc.zmc_eval_samples(zctx.handle, row, s0, 501).astype(np.float64)
@@ -186,6 +187,7 @@ def test_equal_rate_harmonics_single_samples_and_edges(zctx):
     around the quint and chunk boundaries, against the oracle."""
     rng = np.random.default_rng(912)
     ones = _equal_rate_harmonics(1500, rng, 1, 1)
+    assert np.all(zmc.zmc_variant_of(ones)["form"] == 1)
     got = zmc.zmc_integrate(zctx.handle, ones)
     want, _ = oracle.integrate(ones)
     G.compare(ones, got, want)
@@ -245,6 +247,9 @@ def test_abslin_32bit_sum_rows(zctx):
     tab = W.empty(len(rows))
     for i, r in enumerate(rows):
         tab[i] = r
+    # both sums are reached: the 32-bit one from 256 samples on
+    forms = zmc.zmc_variant_of(tab)["form"]
+    assert np.array_equal(forms, (tab["n_samples"] >= 256).astype(forms.dtype))
     got = zmc.zmc_integrate(zctx.handle, tab)
     want, _ = oracle.integrate(tab)
     G.compare(tab, got, want)
