@@ -74,3 +74,16 @@ def test_invalid_rows_are_reported():
         zmc.zmc_variant_of(t)
     assert e.value.status == zmc.ZMC_EINVAL
     assert zmc.zmc_variant_of(W.empty(0)).shape == (0,)
+
+
+def test_random_parity_tables_reach_every_form():
+    """The seeded random tables of the GPU parity sweep (tests/test_gpu_fuzz.py),
+    all together, reach every form the library has."""
+    from tests.test_gpu_fuzz import table
+
+    forms = set()
+    for seed in range(10):
+        v = zmc.zmc_variant_of(table(seed)[0])
+        forms |= {(int(f), int(g)) for f, g in zip(v["family"], v["form"])}
+    assert forms >= {(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1), (3, 2),
+                     (3, 3), (3, 4), (3, 5), (3, 6), (3, 7)}, forms
