@@ -526,6 +526,8 @@ def run_native(args, world, rank, local):
     serving = None
     if rank == 0 and not args.skip_serving:
         serving = run_serving(zmc, local, args.serving_rate, args.serving_seconds)
+        if serving:
+            serving.pop("_stream")
     ctx.close()
 
     if rank != 0:
@@ -706,7 +708,21 @@ def run_serving(zmc, device, rate_hz, seconds, quints_per_lane=0, chunks_per_ite
     return {"rate_jobs_per_s": rate_hz, "jobs": len(lat), "seconds": wall,
             "p50_ms": 1e3 * lat[len(lat) // 2],
             "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "samples_per_s": samples / wall / 1e9, "unit": "Gsamples/s"}
+            "samples_per_s": samples / wall / 1e9, "unit": "Gsamples/s",
+            "_stream": [(at, W.total_samples(tab)) for at, tab in jobs]}
+
+
+def fifo_bound(stream, capacity_gsps):
+    """p50 / p99 latency of an ideal server on the same job stream: jobs served
+    one at a time, oldest first, at capacity_gsps, with no launch granularity
+    (a job's latency is its wait plus its samples / capacity)."""
+    t, lat = 0.0, []
+    for at, n in stream:
+        t = max(t, at) + n / (capacity_gsps * 1e9)
+        lat.append(t - at)
+    lat.sort()
+    return {"capacity_gsps": capacity_gsps, "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
 def run_functional(zmc, ctx):
@@ -893,7 +909,16 @@ def run_serving_sweep(args):
         if r is not None:
             r["demand_gsps"] = rate * 500.5 * 1.444e6 / 1e9  # E[jobs/s x rows x N]
         out.append(r)
-        print(json.dumps({"serving_point": r}), file=sys.stderr, flush=True)
+        print(json.dumps({"serving_point": {k: v for k, v in (r or {}).items() if k != "_stream"}}),
+              file=sys.stderr, flush=True)
+    # the bound at the highest rate the sweep delivered (the capacity, when the
+    # sweep holds a point above it)
+    cap = max((r["samples_per_s"] for r in out if r), default=0.0)
+    for r in out:
+        if r:
+            stream = r.pop("_stream")
+            if cap > 0:
+                r["fifo_bound"] = fifo_bound(stream, cap)
     print(json.dumps({"serving_sweep": out, "seconds_per_rate": args.serving_seconds,
                       "job": "U{1..1000} mixed-style integrands, N ~ 10^U[4,7]"}), flush=True)
 

@@ -8,10 +8,13 @@
 //      admitted jobs: oldest job first by default (each job's next chunks up to
 //      the remaining budget), or equal shares for every job with work left
 //      (zmc_options.serving_share);
-//   3. upload the iteration's entry table and header, replay the iteration graph
-//      (per-family persistent sampling kernels + FP64 merge of every job whose
-//      last chunks ran), copy those jobs' results to pinned staging, record an
-//      event; two iteration slots are in flight at once;
+//   3. upload the iteration's entry table and header on the copy-in stream (so
+//      the copies overlap the launch before), replay the iteration graph (the
+//      per-family persistent sampling kernels) on the sampling stream, and on a
+//      side stream, after the graph, merge (FP64) every job whose last chunks
+//      ran and copy those jobs' results to pinned staging, record an event; the
+//      sampling stream goes straight on to the next graph, so the merge and the
+//      copies overlap the next launch; two iteration slots are in flight at once;
 //   4. when a slot's event completes, hand the finished jobs' results to
 //      zmc_poll and free their device blocks.
 // Checkpoints: zmc_checkpoint takes a running job off the live list; the next
@@ -80,7 +83,9 @@ struct Slot {
   const FnDev **d_merge = nullptr;
   zmc_result *d_results = nullptr;  // contiguous copy target of merged results
   char *h_stage = nullptr;          // pinned: entries | merge list | hdr | results
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;      // the slot's last work (side stream): results staged
+  cudaEvent_t ev_up = nullptr;   // its tables uploaded (copy-in stream)
+  cudaEvent_t ev_run = nullptr;  // its sampling graph done (sampling stream)
   cudaGraphExec_t graph = nullptr;
   bool busy = false;
   uint64_t seq = 0;
@@ -104,7 +109,9 @@ struct ServingState {
   std::unordered_map<uint64_t, std::shared_ptr<ServJob>> jobs;
   std::vector<std::shared_ptr<ServJob>> cancelled_pending;
   uint64_t next_id = 1;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // sampling graphs, back to back
+  cudaStream_t up = nullptr;      // host -> device tables
+  cudaStream_t side = nullptr;    // merges and device -> host results
   FamilyFork fork;  // the four family kernels of an iteration run concurrently
   Slot slots[2];
   uint32_t max_chunks = 0;
@@ -154,7 +161,7 @@ bool try_admit(ServingState *S, const std::shared_ptr<ServJob> &jp, char *stage,
   char *src = stage + stage_used;
   std::memcpy(src, j.fns.data(), tbytes);
   stage_used += round256(tbytes);
-  cudaError_t e = cudaMemcpyAsync(j.d_fns, src, tbytes, cudaMemcpyHostToDevice, S->stream);
+  cudaError_t e = cudaMemcpyAsync(j.d_fns, src, tbytes, cudaMemcpyHostToDevice, S->up);
   if (e != cudaSuccess) {
     ctx_cuda_fail(ctx, e, "serving admission upload");
     S->thread_status = ZMC_ECUDA;
@@ -175,11 +182,6 @@ zmc_status build_slot_graph(ServingState *S, Slot &sl) {
                              ctx->shape.block};
   if (le == cudaSuccess)
     le = launch_families(S->fork, sl.d_entries, sl.d_hdr, S->grid, block, all, S->stream);
-  if (le == cudaSuccess) {
-    const unsigned mg = static_cast<unsigned>(
-        std::min<uint64_t>((S->max_merge + 7) / 8, static_cast<uint64_t>(ctx->sms) * 16));
-    le = launch_merge(sl.d_merge, sl.d_hdr, mg, S->stream);
-  }
   e = cudaStreamEndCapture(S->stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -470,6 +472,8 @@ void scheduler_loop(ServingState *S) {
         mrg[nm + i] = j->d_fns + i;
       }
       used += round256(tbytes);
+      // on the sampling stream: the launches that ran the job's chunks read the
+      // table being rewritten, and they run before this copy
       cudaError_t e = cudaMemcpyAsync(j->d_fns, cut, tbytes, cudaMemcpyHostToDevice, S->stream);
       if (e != cudaSuccess) {
         ctx_cuda_fail(ctx, e, "serving checkpoint upload");
@@ -506,22 +510,35 @@ void scheduler_loop(ServingState *S) {
       S->thread_status = ZMC_ECUDA;
       continue;
     }
+    // the slot's buffers were last read by its previous iteration, which has
+    // retired (its merge and copies included)
     if (k > 0)
       e = cudaMemcpyAsync(slot->d_entries, ents, k * sizeof(Entry), cudaMemcpyHostToDevice,
-                          S->stream);
+                          S->up);
     if (e == cudaSuccess && nm > 0)
       e = cudaMemcpyAsync(slot->d_merge, mrg, nm * sizeof(FnDev *), cudaMemcpyHostToDevice,
-                          S->stream);
+                          S->up);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(slot->d_hdr, hdr, sizeof(LaunchHdr), cudaMemcpyHostToDevice, S->stream);
+      e = cudaMemcpyAsync(slot->d_hdr, hdr, sizeof(LaunchHdr), cudaMemcpyHostToDevice, S->up);
+    if (e == cudaSuccess) e = cudaEventRecord(slot->ev_up, S->up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->stream, slot->ev_up, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(slot->graph, S->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(slot->ev_run, S->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->side, slot->ev_run, 0);
+    if (e == cudaSuccess && nm > 0) {
+      // the jobs merged here have no chunks in later launches, so the merge
+      // overlaps the next sampling graph
+      const unsigned mg = static_cast<unsigned>(
+          std::min<uint64_t>((nm + 7) / 8, static_cast<uint64_t>(ctx->sms) * 16));
+      e = launch_merge(slot->d_merge, slot->d_hdr, mg, S->side);
+    }
     char *res_stage = st + ent_bytes + mrg_bytes + hdr_bytes;
     for (size_t q = 0; e == cudaSuccess && q < slot->finishing.size(); ++q) {
       auto &j = slot->finishing[q];
       e = cudaMemcpyAsync(res_stage + slot->result_off[q] * sizeof(zmc_result), j->d_out,
-                          j->n * sizeof(zmc_result), cudaMemcpyDeviceToHost, S->stream);
+                          j->n * sizeof(zmc_result), cudaMemcpyDeviceToHost, S->side);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(slot->ev, S->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(slot->ev, S->side);
     if (e != cudaSuccess) {
       ctx_cuda_fail(ctx, e, "serving iteration");
       S->thread_status = ZMC_ECUDA;
@@ -550,6 +567,8 @@ zmc_status serving_start(zmc_ctx *ctx) {
   S->max_merge = 1u << 16;
   if (const char *f = std::getenv("ZMC_SERVING_FAULT_AT")) S->fault_at = std::strtoull(f, nullptr, 10);
   cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->up, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving stream");
   e = S->fork.init();
   if (e != cudaSuccess) {
@@ -567,6 +586,8 @@ zmc_status serving_start(zmc_ctx *ctx) {
     e = cudaHostAlloc(reinterpret_cast<void **>(&sl.h_stage), sb, cudaHostAllocDefault);
     if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving staging");
     e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_up, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_run, cudaEventDisableTiming);
     if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "serving event");
     zmc_status st = build_slot_graph(S.get(), sl);
     if (st != ZMC_OK) return st;
@@ -596,17 +617,23 @@ void serving_stop(zmc_ctx *ctx) {
   S->cv_work.notify_all();
   S->cv_done.notify_all();
   if (S->thread.joinable()) S->thread.join();
+  cudaStreamSynchronize(S->up);
   cudaStreamSynchronize(S->stream);
+  cudaStreamSynchronize(S->side);
   for (auto &kv : S->jobs) free_job_device(S, *kv.second);
   for (auto &sl : S->slots) {
     if (sl.graph) cudaGraphExecDestroy(sl.graph);
     if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.ev_up) cudaEventDestroy(sl.ev_up);
+    if (sl.ev_run) cudaEventDestroy(sl.ev_run);
     if (sl.h_stage) cudaFreeHost(sl.h_stage);
     ctx->arena.release(sl.d_entries);
     ctx->arena.release(sl.d_merge);
     ctx->arena.release(sl.d_hdr);
   }
   cudaStreamDestroy(S->stream);
+  cudaStreamDestroy(S->up);
+  cudaStreamDestroy(S->side);
   S->fork.destroy();
   delete S;
   ctx->srv = nullptr;
