@@ -641,6 +641,11 @@ def batched_and_plain(zmc, torch, ctx, table, flush, name, steps, plain):
            "batched_ms": statistics.median(st)}
     res = zmc.zmc_plan_results(plan, len(table))
     assert np.all(res["status"] == 0)
+    pi = zmc.zmc_plan_info_get(plan)
+    out["plan"] = {"quints_per_lane": pi["quints_per_lane"],
+                   "unroll": list(pi["family_unroll"]),
+                   "chunk_tune": {0: "default", 1: "measured", 2: "cached"}.get(
+                       pi["chunk_tune_source"], pi["chunk_tune_source"])}
     if plain:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         zmc.zmc_plan_run_plain(plan)

@@ -653,6 +653,7 @@ zmc_status plan_build(zmc_ctx *ctx, const zmc_desc *desc, size_t n, zmc_plan **o
                       const uint64_t *s_begin = nullptr, const uint64_t *s_end = nullptr,
                       const PlanChoice *force = nullptr, bool wait_upload = true);
 void plan_free(zmc_plan *plan);
+zmc_status plan_enqueue(zmc_plan *plan, uint32_t stages);
 
 // The key of a table's shape class for the chunk tuner: the GPU, the families
 // present with their dominant dimension and kernels' registers, and the
@@ -704,17 +705,47 @@ zmc_status time_family(zmc_plan *plan, int f, int unroll, cudaEvent_t e0, cudaEv
   return ZMC_OK;
 }
 
+// Device time of a plan's sampling stage as a plan runs it (the family kernels
+// concurrently): the best of two launches after a warm-up (milliseconds).
+zmc_status time_plan_sample(zmc_plan *plan, cudaEvent_t e0, cudaEvent_t e1, float *ms_out) {
+  zmc_ctx *ctx = plan->ctx;
+  cudaStream_t str = ctx->stream;
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaError_t e = cudaEventRecord(e0, str);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "chunk autotune");
+    const zmc_status st = plan_enqueue(plan, ZMC_STAGE_SAMPLE);
+    if (st != ZMC_OK) return st;
+    e = cudaEventRecord(e1, str);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "chunk autotune");
+    if (rep > 0) best = std::min(best, ms);
+  }
+  *ms_out = best;
+  return ZMC_OK;
+}
+
 // Samples and rows of the table subset the chunk tuner times each candidate on.
 constexpr double kTrialSamples = 2147483648.0;
 constexpr size_t kTrialRows = 1u << 16;
 
-// Chunk tuner: the chunk length (kTuneQuints) and per-family unroll under which
-// a bounded subset of the table's rows (every k-th row, whole rows; at most
-// ~2^31 samples and 2^16 rows) samples fastest, or the cached choice for the
-// table's shape class.  Each candidate
-// chunk length builds a trial plan of the subset; each family kernel present is
-// timed alone at both unrolls.  *source: 1 measured, 2 cached, 0 left at the
-// defaults (a trial plan did not fit the arena).
+// Chunk tuner: the chunk length (kTuneQuints) and per-family unroll for a
+// table, or the cached choice for the table's shape class.  The candidates are
+// timed on a bounded subset of the table's rows (every k-th row, whole rows; at
+// most ~2^31 samples and 2^16 rows), as a plan runs it (every family kernel at
+// once, unroll 1).  When the subset is not the whole table, its time is carried
+// over to the table by a straight line through two subsets, every 2k-th and
+// every k-th row: T(samples) = O + b * samples, predicted = O + b *
+// samples(table).  The fixed part O (the kernels draining their last chunks at
+// each change of family and at the end; on the 10^4-integrand mix 1.4 to 7
+// chunk times, growing with the chunk length) weighs several times more in a
+// subset than in the table, and scaling the subset's time alone picked chunks
+// of 52 quints where 208 ran the table 1.8% faster.  Then, at the chosen length,
+// each family kernel present is timed alone at both unrolls (their fixed parts
+// are alike).  *source: 1 measured, 2 cached, 0 left at the defaults (no trial
+// plan fitted the arena).
 zmc_status choose_chunk(zmc_ctx *ctx, const zmc_desc *desc, size_t n, PlanChoice *choice,
                         int *source) {
   const std::string key = chunk_tune_key(ctx, desc, n);
@@ -730,8 +761,19 @@ zmc_status choose_chunk(zmc_ctx *ctx, const zmc_desc *desc, size_t n, PlanChoice
   const size_t stride = std::max<size_t>(
       total <= kTrialSamples ? 1 : static_cast<size_t>(std::ceil(total / kTrialSamples)),
       (n + kTrialRows - 1) / kTrialRows);
-  std::vector<zmc_desc> sub;
-  for (size_t i = 0; i < n; i += stride) sub.push_back(desc[i]);
+  std::vector<zmc_desc> sub, half;  // every stride-th row; every 2 stride-th row
+  double sub_total = 0.0, half_total = 0.0;
+  for (size_t i = 0; i < n; i += stride) {
+    sub.push_back(desc[i]);
+    sub_total += static_cast<double>(desc[i].n_samples);
+    if ((i / stride) % 2 == 0) {
+      half.push_back(desc[i]);
+      half_total += static_cast<double>(desc[i].n_samples);
+    }
+  }
+  // a line needs two subsets of different size, and is not needed when the
+  // subset is the table
+  const bool extrapolate = stride > 1 && half_total < sub_total;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ZMC_CUDA(ctx, cudaEventCreate(&e0));
   cudaError_t ce = cudaEventCreate(&e1);
@@ -740,8 +782,9 @@ zmc_status choose_chunk(zmc_ctx *ctx, const zmc_desc *desc, size_t n, PlanChoice
     return ctx_cuda_fail(ctx, ce, "chunk autotune");
   }
   zmc_status st = ZMC_OK;
-  float best_total = 1e30f;
+  double best_pred = 1e300;
   TuneChoice best;
+  zmc_plan *best_trial = nullptr;
   for (uint32_t q : kTuneQuints) {
     PlanChoice trial_choice{q, {1, 1, 1, 1}};
     zmc_plan *trial = nullptr;
@@ -751,30 +794,52 @@ zmc_status choose_chunk(zmc_ctx *ctx, const zmc_desc *desc, size_t n, PlanChoice
       continue;
     }
     if (st != ZMC_OK) break;
-    float sum = 0.0f;
-    unsigned u_best[4] = {1, 1, 1, 1};
-    for (int f = 0; f < 4 && st == ZMC_OK; ++f) {
-      if (trial->fam_items[f] == 0) continue;
-      float t_best = 1e30f;
-      for (int u = 1; u <= kMaxUnroll && st == ZMC_OK; ++u) {
-        float ms = 0.0f;
-        st = time_family(trial, f, u, e0, e1, &ms);
-        if (ms < t_best) {
-          t_best = ms;
-          u_best[f] = static_cast<unsigned>(u);
-        }
+    float ms = 0.0f;
+    st = time_plan_sample(trial, e0, e1, &ms);
+    double pred = ms;
+    if (st == ZMC_OK && extrapolate) {
+      zmc_plan *trial_half = nullptr;
+      st = plan_build(ctx, half.data(), half.size(), &trial_half, nullptr, nullptr,
+                      &trial_choice);
+      float ms_half = 0.0f;
+      if (st == ZMC_OK) {
+        st = time_plan_sample(trial_half, e0, e1, &ms_half);
+        plan_free(trial_half);
+        const double b = (static_cast<double>(ms) - ms_half) / (sub_total - half_total);
+        pred = ms + b * (total - sub_total);
+      } else if (st == ZMC_ENOMEM) {  // no room for the second subset: scale the first
+        st = ZMC_OK;
+        pred = ms * total / sub_total;
       }
-      sum += t_best;
     }
-    plan_free(trial);
-    if (st != ZMC_OK) break;
-    if (sum < best_total) {
-      best_total = sum;
+    if (st != ZMC_OK) {
+      plan_free(trial);
+      break;
+    }
+    if (pred < best_pred) {
+      best_pred = pred;
       best.quints = q;
-      for (int f = 0; f < 4; ++f) best.unroll[f] = u_best[f];
-      best.ms = sum;
+      best.ms = static_cast<float>(pred);
+      if (best_trial) plan_free(best_trial);
+      best_trial = trial;
+    } else {
+      plan_free(trial);
     }
   }
+  // the unroll of each family kernel at the chosen chunk length
+  for (int f = 0; f < 4 && st == ZMC_OK && best_trial; ++f) {
+    if (best_trial->fam_items[f] == 0) continue;
+    float t_best = 1e30f;
+    for (int u = 1; u <= kMaxUnroll && st == ZMC_OK; ++u) {
+      float ms = 0.0f;
+      st = time_family(best_trial, f, u, e0, e1, &ms);
+      if (ms < t_best) {
+        t_best = ms;
+        best.unroll[f] = static_cast<unsigned>(u);
+      }
+    }
+  }
+  if (best_trial) plan_free(best_trial);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != ZMC_OK) return st;
