@@ -129,7 +129,8 @@ typedef struct zmc_options {
                                     256-byte aligned; NULL -> the library allocates */
     void *stream;                /* cudaStream_t for all work; NULL -> the library
                                     creates a non-blocking stream                   */
-    uint32_t max_chunks_per_iter;/* serving: chunks per persistent launch; 0 -> auto */
+    uint32_t max_chunks_per_iter;/* serving: chunks per persistent launch; 0 -> the
+                                    chunks of 2^31 samples                          */
     uint32_t autotune;           /* flags (0: none):
                                     ZMC_TUNE_GEOMETRY: time launch geometries of each
                                     family kernel on a slice of a new plan's work (or
@@ -158,6 +159,16 @@ typedef struct zmc_options {
                                     launch's budget, what is left to the next job);
                                     > 0: an equal share for every job with work
                                     left, at least this many chunks each          */
+    uint32_t reserved;
+    uint64_t serving_cut_backlog;/* serving, oldest first: while fewer than this
+                                    many samples are left to issue over the live
+                                    jobs, a launch ends with the last chunks of the
+                                    first job it completes (that job's results do
+                                    not wait for newer jobs' chunks; they start the
+                                    next launch); with a longer backlog every launch
+                                    is filled to its budget.  0 -> 2^34 (about 47 ms
+                                    of sampling on one GB300); 1 -> every launch
+                                    filled.  Results do not depend on it.          */
 } zmc_options;
 
 #define ZMC_TUNE_GEOMETRY 1u

@@ -1222,6 +1222,7 @@ zmc_status zmc_create(const zmc_options *opt_in, zmc_ctx **out) {
   ctx->quints_per_lane = opt.quints_per_lane;
   ctx->max_chunks_per_iter = opt.max_chunks_per_iter;
   ctx->serving_share = opt.serving_share;
+  ctx->serving_cut_backlog = opt.serving_cut_backlog ? opt.serving_cut_backlog : (1ull << 34);
   ctx->autotune = opt.autotune;
   if (opt.tune_cache_path) ctx->tune_cache_path = opt.tune_cache_path;
   tune_cache_load(ctx.get());

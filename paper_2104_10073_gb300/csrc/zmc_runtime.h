@@ -105,6 +105,7 @@ struct zmc_ctx {
   uint32_t quints_per_lane = 16;
   uint32_t max_chunks_per_iter = 0;
   uint32_t serving_share = 0;  // serving: 0 oldest job first, > 0 equal shares of >= this
+  uint64_t serving_cut_backlog = 0;  // serving: backlog below which launches end at a job
   uint32_t autotune = 0;  // ZMC_TUNE_* flags
   std::string tune_cache_path;
   zmc::LaunchShape shape;

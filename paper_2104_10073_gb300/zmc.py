@@ -47,7 +47,8 @@ class zmc_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("max_chunks_per_iter", ctypes.c_uint32),
                 ("autotune", ctypes.c_uint32), ("device", ctypes.c_int32),
                 ("quints_per_lane", ctypes.c_uint32), ("tune_cache_path", ctypes.c_char_p),
-                ("serving", ctypes.c_uint32), ("serving_share", ctypes.c_uint32)]
+                ("serving", ctypes.c_uint32), ("serving_share", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("serving_cut_backlog", ctypes.c_uint64)]
 
 
 class zmc_plan_info(ctypes.Structure):
@@ -540,6 +541,7 @@ class Context:
     def __init__(self, arena_bytes: int = 1 << 30, device: int = 0, stream=None,
                  serving: bool = False, quints_per_lane: int = 0,
                  max_chunks_per_iter: int = 0, serving_share: int = 0,
+                 serving_cut_backlog: int = 0,
                  use_torch_memory: bool = True, autotune: bool | int = False,
                  tune_cache_path: str | None = None):
         import torch
@@ -555,6 +557,7 @@ class Context:
         opt.quints_per_lane = quints_per_lane
         opt.max_chunks_per_iter = max_chunks_per_iter
         opt.serving_share = serving_share
+        opt.serving_cut_backlog = serving_cut_backlog
         # True: launch geometry only; an int: ZMC_TUNE_* flags
         opt.autotune = (ZMC_TUNE_GEOMETRY if autotune is True
                         else int(autotune) if autotune else 0)

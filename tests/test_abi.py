@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes(lib):
     assert lib.zmc_desc_size() == 464 == W.DESC_DTYPE.itemsize
     assert lib.zmc_result_size() == 32 == zmc.RESULT_DTYPE.itemsize
-    assert ctypes.sizeof(zmc.zmc_options) == 56
+    assert ctypes.sizeof(zmc.zmc_options) == 72
     offs = {n: W.DESC_DTYPE.fields[n][1] for n in W.DESC_DTYPE.names}
     assert offs == {"family": 0, "dim": 4, "stream_id": 8, "deg": 12, "n_samples": 16,
                     "seed": 24, "lo": 32, "hi": 88, "p": 144}

@@ -17,8 +17,10 @@ def sctx():
     from paper_2104_10073_gb300 import build
 
     build.build()
-    # small iterations so that jobs interleave across many launches
-    c = zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=4096)
+    # small iterations so that jobs interleave across many launches, every launch
+    # filled to its budget (no launch ends early at a job's last chunks)
+    c = zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=4096,
+                    serving_cut_backlog=1)
     yield c
     c.close()
 
@@ -84,6 +86,44 @@ def test_results_same_under_both_share_policies(sctx):
             assert np.array_equal(res["estimate"], a["estimate"])
             assert np.array_equal(res["stderr"], a["stderr"], equal_nan=True)
         assert zmc.zmc_serving_stats_get(eq.handle)["shared_iterations"] >= 1
+
+
+def test_short_backlog_ends_launches_at_job_ends(sctx):
+    """Oldest first, launches end with the first job they complete while the
+    backlog is short, and are filled (several jobs sharing one) while it is long;
+    results are the same bit for bit under either rule."""
+    # a long first job (2^32 samples, ~250 launches here) holds the GPU while the
+    # others queue behind it, so the backlog is known when their launches are built
+    blocker = W.empty(1)
+    W.harmonic(blocker[0], 1.0, 0.5, [3.0], [0.0], [1.0], 2**32, seed=99)
+    jobs = [blocker] + _jobs(10, seed=31, max_fns=40, hi_exp=6.0)
+    ids = [zmc.zmc_submit(sctx.handle, t) for t in jobs]
+    filled = [zmc.zmc_poll(sctx.handle, j, len(t), wait_ms=-1)[1] for j, t in zip(ids, jobs)]
+    rest = sum(W.total_samples(t) for t in jobs[1:])
+    # the library default (2^34 samples) is above this stream's whole backlog:
+    # every launch ends at a job's end, so no launch holds chunks of two jobs
+    with zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=4096) as c:
+        ids = [zmc.zmc_submit(c.handle, t) for t in jobs]
+        for j, t, a in zip(ids, jobs, filled):
+            st, res = zmc.zmc_poll(c.handle, j, len(t), wait_ms=-1)
+            assert st == zmc.ZMC_OK
+            assert np.array_equal(res["estimate"], a["estimate"])
+            assert np.array_equal(res["stderr"], a["stderr"], equal_nan=True)
+        stats = zmc.zmc_serving_stats_get(c.handle)
+        assert stats["max_jobs_per_iter"] == 1 and stats["shared_iterations"] == 0
+    # a threshold below the backlog behind the first job: the launches that
+    # finish the first job and start the queued ones are filled and shared; the
+    # last ones (short backlog) end at job ends
+    with zmc.Context(arena_bytes=1 << 30, serving=True, max_chunks_per_iter=4096,
+                     serving_cut_backlog=rest // 3) as c:
+        ids = [zmc.zmc_submit(c.handle, t) for t in jobs]
+        for j, t, a in zip(ids, jobs, filled):
+            st, res = zmc.zmc_poll(c.handle, j, len(t), wait_ms=-1)
+            assert st == zmc.ZMC_OK
+            assert np.array_equal(res["estimate"], a["estimate"])
+        stats = zmc.zmc_serving_stats_get(c.handle)
+        assert stats["shared_iterations"] >= 1
+        assert stats["iterations"] > stats["shared_iterations"]
 
 
 def test_poll_semantics(sctx):
