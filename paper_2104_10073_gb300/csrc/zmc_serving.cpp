@@ -32,6 +32,7 @@
 // mixed with others.  No kernel waits on another: every launch drains a finite
 // work list and exits.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -102,6 +103,7 @@ struct ServingState {
   std::condition_variable cv_work;
   std::condition_variable cv_done;
   bool stop = false;
+  std::atomic<uint64_t> submits{0};  // jobs queued so far (read without the lock)
   std::deque<std::shared_ptr<ServJob>> queue;
   std::vector<std::shared_ptr<ServJob>> live;
   std::deque<std::shared_ptr<ServJob>> to_merge;
@@ -322,12 +324,22 @@ void scheduler_loop(ServingState *S) {
       bool any_busy = S->slots[0].busy || S->slots[1].busy;
       if (S->stop && !any_busy) return;
       if (any_busy) {
+        const uint64_t seen = S->submits.load(std::memory_order_acquire);
         lk.unlock();
-        // wait for the oldest busy slot outside the lock
+        // wait outside the lock for the oldest busy slot, or, when a slot is
+        // free, for the first of that slot's completion and a new job: a job
+        // that arrives while one launch runs is then built and queued behind it
+        // at once instead of after the launch's results have been copied back
         Slot *oldest = nullptr;
         for (auto &sl : S->slots)
           if (sl.busy && (!oldest || sl.seq < oldest->seq)) oldest = &sl;
-        if (oldest) cudaEventSynchronize(oldest->ev);
+        if (oldest && !slot) {
+          cudaEventSynchronize(oldest->ev);
+        } else if (oldest) {
+          while (cudaEventQuery(oldest->ev) == cudaErrorNotReady &&
+                 S->submits.load(std::memory_order_acquire) == seen)
+            std::this_thread::yield();
+        }
         continue;
       }
       if (!S->queue.empty()) {
@@ -720,6 +732,7 @@ zmc_status submit_job(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *fro
     j->id = S->next_id++;
     S->jobs[j->id] = j;
     S->queue.push_back(j);
+    S->submits.fetch_add(1, std::memory_order_release);
     S->stats.submitted++;
     *job_id = j->id;
   }
