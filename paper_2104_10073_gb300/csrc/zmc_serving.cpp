@@ -103,7 +103,7 @@ struct ServingState {
   std::condition_variable cv_work;
   std::condition_variable cv_done;
   bool stop = false;
-  std::atomic<uint64_t> submits{0};  // jobs queued so far (read without the lock)
+  std::atomic<uint64_t> wakeups{0};  // new work announced (submits, checkpoints)
   std::deque<std::shared_ptr<ServJob>> queue;
   std::vector<std::shared_ptr<ServJob>> live;
   std::deque<std::shared_ptr<ServJob>> to_merge;
@@ -324,12 +324,13 @@ void scheduler_loop(ServingState *S) {
       bool any_busy = S->slots[0].busy || S->slots[1].busy;
       if (S->stop && !any_busy) return;
       if (any_busy) {
-        const uint64_t seen = S->submits.load(std::memory_order_acquire);
+        const uint64_t seen = S->wakeups.load(std::memory_order_acquire);
         lk.unlock();
         // wait outside the lock for the oldest busy slot, or, when a slot is
-        // free, for the first of that slot's completion and a new job: a job
-        // that arrives while one launch runs is then built and queued behind it
-        // at once instead of after the launch's results have been copied back
+        // free, for the first of that slot's completion and new work (a job, a
+        // checkpoint): a job that arrives while one launch runs is then built
+        // and queued behind it at once instead of after the launch's results
+        // have been copied back
         Slot *oldest = nullptr;
         for (auto &sl : S->slots)
           if (sl.busy && (!oldest || sl.seq < oldest->seq)) oldest = &sl;
@@ -337,7 +338,7 @@ void scheduler_loop(ServingState *S) {
           cudaEventSynchronize(oldest->ev);
         } else if (oldest) {
           while (cudaEventQuery(oldest->ev) == cudaErrorNotReady &&
-                 S->submits.load(std::memory_order_acquire) == seen)
+                 S->wakeups.load(std::memory_order_acquire) == seen)
             std::this_thread::yield();
         }
         continue;
@@ -732,7 +733,7 @@ zmc_status submit_job(zmc_ctx *ctx, const zmc_desc *desc, const zmc_moments *fro
     j->id = S->next_id++;
     S->jobs[j->id] = j;
     S->queue.push_back(j);
-    S->submits.fetch_add(1, std::memory_order_release);
+    S->wakeups.fetch_add(1, std::memory_order_release);
     S->stats.submitted++;
     *job_id = j->id;
   }
@@ -838,6 +839,7 @@ zmc_status zmc_checkpoint(zmc_ctx *ctx, uint64_t job_id, zmc_moments *out, int32
       j->state = JobState::kCheckpointing;
       S->live.erase(std::remove(S->live.begin(), S->live.end(), j), S->live.end());
       S->to_ckpt.push_back(j);
+      S->wakeups.fetch_add(1, std::memory_order_release);
       S->cv_work.notify_one();
       break;
     case JobState::kCheckpointing:
