@@ -264,10 +264,13 @@ zmc_status zmc_integrate_functional(zmc_ctx *ctx, const zmc_desc *base, const ui
 
 /* Serving (continuous batching).  zmc_submit copies the n descriptors into a
  * job and returns its id at once; the scheduler admits queued jobs as device
- * memory frees up, keeps their partial sums on the device, and gives every
- * persistent launch a share of the chunks of every admitted job.  A job that
- * alone exceeds the memory budget is refused with ZMC_ENOMEM; a job may hold at
- * most 43690 integrands (ZMC_EINVAL beyond).
+ * memory frees up, keeps their partial sums on the device, and fills each
+ * persistent launch with the admitted jobs' chunks, oldest job first (or in
+ * equal shares, opt->serving_share); while the backlog is short a launch ends
+ * with the first job it completes (opt->serving_cut_backlog).  A job's results
+ * do not depend on which jobs share its launches.  A job that alone exceeds the
+ * memory budget is refused with ZMC_ENOMEM; a job may hold at most 43690
+ * integrands (ZMC_EINVAL beyond).
  * Requires opt->serving = 1. */
 zmc_status zmc_submit(zmc_ctx *ctx, const zmc_desc *desc, size_t n, uint64_t *job_id);
 
