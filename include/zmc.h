@@ -541,6 +541,24 @@ zmc_status zmc_validate(const zmc_desc *desc, size_t n, size_t *bad_index);
  * (tests use this to check that their tables reach every form). */
 zmc_status zmc_variant_of(const zmc_desc *desc, size_t n, uint32_t *forms, size_t *bad_index);
 
+/* The serving scheduler's rule for filling one persistent launch (host only; no
+ * GPU or context needed, so the rule can be checked anywhere).  Job i is the
+ * i-th oldest live job and has chunks_left[i] chunks of chunk_samples samples
+ * left to issue; on return take[i] holds the chunks it contributes to a launch
+ * of at most budget chunks (sum take <= budget, take[i] <= chunks_left[i]).
+ *   share == 0 (oldest first): each job in turn takes its remaining chunks up
+ *     to what is left of the budget; if the backlog, sum chunks_left[i] *
+ *     chunk_samples, is below cut_backlog, the launch ends with the first job
+ *     it completes (cut_backlog 0: never);
+ *   share > 0 (equal shares): passes over the jobs with work left, each taking
+ *     up to max(share, budget left / jobs with work left) per pass, until the
+ *     budget or the work runs out.
+ * Layouts: chunks_left and take hold n_jobs values (caller-owned).  Errors:
+ * ZMC_EINVAL for a NULL array with n_jobs > 0 or chunk_samples == 0. */
+zmc_status zmc_serving_fill(const uint64_t *chunks_left, size_t n_jobs, uint64_t budget,
+                            uint32_t share, uint64_t cut_backlog, uint64_t chunk_samples,
+                            uint64_t *take);
+
 /* sizeof checks for foreign-language bindings. */
 size_t zmc_desc_size(void);
 size_t zmc_result_size(void);

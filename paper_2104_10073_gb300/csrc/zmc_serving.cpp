@@ -258,6 +258,56 @@ void retire_slot(ServingState *S, Slot &sl) {
   S->cv_done.notify_all();
 }
 
+// The launch fill rule (zmc_serving_fill): take[i] chunks of job i, jobs in
+// arrival order.  Oldest first by default: each job takes its next chunks up to
+// the whole remaining budget, so a launch finishes the oldest jobs and starts
+// the next ones with what is left (measured on the Poisson job stream: p99
+// latency 17 ms instead of 22 ms at 300 jobs/s, 33 instead of 53 ms at 400, p50
+// unchanged, against equal shares).  With a short backlog (fewer than
+// cut_backlog samples left to issue over the jobs) the launch ends with the
+// last chunks of the first job it completes, so that job's results do not wait
+// for the newer jobs' chunks behind it; those start the next launch, which runs
+// right after it.  With a long backlog every launch is filled (each launch
+// costs a fixed ~50 us).  Measured (2^31-sample budget): p99 15.4 against 16.7
+// ms at 300 jobs/s, 29.9 against 30.6 at 400, 364 against 360 G samples/s under
+// overload.  With share > 0 every job with work left gets budget / jobs per
+// pass, but at least share chunks (runs of a few chunks would turn every work
+// item into an entry-table search).
+void fill_launch(const uint64_t *left, size_t n, uint64_t budget, uint64_t share,
+                 uint64_t cut_backlog, uint64_t chunk_samples, uint64_t *take) {
+  for (size_t i = 0; i < n; ++i) take[i] = 0;
+  if (share == 0) {
+    uint64_t backlog = 0;  // saturating: a job may hold up to 2^62 samples per row
+    for (size_t i = 0; i < n && backlog != UINT64_MAX; ++i) {
+      const uint64_t s = left[i] > UINT64_MAX / chunk_samples ? UINT64_MAX
+                                                               : left[i] * chunk_samples;
+      backlog = backlog > UINT64_MAX - s ? UINT64_MAX : backlog + s;
+    }
+    const bool cut = backlog < cut_backlog;
+    for (size_t i = 0; i < n && budget > 0; ++i) {
+      take[i] = std::min(left[i], budget);
+      budget -= take[i];
+      if (cut && take[i] > 0 && take[i] == left[i]) break;
+    }
+    return;
+  }
+  std::vector<size_t> active;
+  for (size_t i = 0; i < n; ++i)
+    if (left[i] > 0) active.push_back(i);
+  while (budget > 0 && !active.empty()) {
+    const uint64_t per = std::max<uint64_t>(share, budget / active.size());
+    std::vector<size_t> still;
+    for (size_t i : active) {
+      const uint64_t t = std::min({per, budget, left[i] - take[i]});
+      take[i] += t;
+      budget -= t;
+      if (take[i] < left[i]) still.push_back(i);
+      if (budget == 0) break;
+    }
+    active.swap(still);
+  }
+}
+
 void scheduler_loop(ServingState *S) {
   zmc_ctx *ctx = S->ctx;
   cudaSetDevice(ctx->device);
@@ -362,76 +412,47 @@ void scheduler_loop(ServingState *S) {
         st + round256(S->max_entries * sizeof(Entry)) + round256(S->max_merge * sizeof(FnDev *)));
     std::vector<Entry> fam_ents[4];
     std::unordered_map<const FnDev *, uint32_t> variant_of;
-    uint64_t budget = S->max_chunks;
-    // fair share: equal split, leftovers handed out on further passes
+    // the launch's chunks per live job (fill_launch); a run of chunks of one
+    // integrand is one entry, so the entry table never holds more entries than
+    // the launch has chunks
     std::vector<std::shared_ptr<ServJob>> active;
     for (auto &j : S->live)
       if (j->state == JobState::kRunning && j->chunks_issued < j->chunks_total) active.push_back(j);
+    std::vector<uint64_t> left(active.size()), take(active.size());
+    for (size_t q = 0; q < active.size(); ++q)
+      left[q] = active[q]->chunks_total - active[q]->chunks_issued;
+    fill_launch(left.data(), active.size(), std::min<uint64_t>(S->max_chunks, S->max_entries),
+                ctx->serving_share, ctx->serving_share ? 0 : ctx->serving_cut_backlog,
+                chunk_samples_of(ctx->quints_per_lane), take.data());
     uint32_t n_entries = 0;
     uint64_t jobs_in_iter = 0;  // jobs with work items in this launch
-    // Jobs are visited oldest first.  By default each takes its next chunks up
-    // to the whole remaining budget, so a launch finishes the oldest jobs and
-    // starts the next ones with what is left (measured on the Poisson job
-    // stream: p99 latency 17 ms instead of 22 ms at 300 jobs/s, 33 instead of
-    // 53 ms at 400, p50 unchanged).  With zmc_options.serving_share > 0 every
-    // job with work left gets budget / active chunks, but at least that floor
-    // (runs of a few chunks would turn every work item into an entry-table
-    // search).
-    const uint64_t min_share = ctx->serving_share ? ctx->serving_share : ~0ull;
-    // Oldest first with a short backlog (fewer than serving_cut_backlog samples
-    // left to issue over the live jobs): the launch ends with the last chunks of
-    // the first job it completes, so that job's results do not wait for the
-    // newer jobs' chunks behind it; those start the next launch, which runs
-    // right after it.  With a long backlog every launch is filled (each launch
-    // costs a fixed ~50 us).  Measured on the Poisson job stream (2^31-sample
-    // budget): p99 15.4 against 16.7 ms at 300 jobs/s, 29.9 against 30.6 at 400,
-    // 364 against 360 G samples/s under overload.
-    bool cut_at_job_end = false;
-    if (!ctx->serving_share) {
-      const uint64_t cs = chunk_samples_of(ctx->quints_per_lane);
-      uint64_t backlog = 0;
-      for (auto &j : active) backlog += (j->chunks_total - j->chunks_issued) * cs;
-      cut_at_job_end = backlog < ctx->serving_cut_backlog;
-    }
-    while (budget > 0 && !active.empty() && n_entries < S->max_entries) {
-      const uint64_t share = std::max<uint64_t>(min_share, budget / active.size());
-      std::vector<std::shared_ptr<ServJob>> still;
-      for (auto &j : active) {
-        uint64_t take = std::min<uint64_t>(share, budget);
-        if (j->last_seq != seq && take > 0) ++jobs_in_iter;
-        while (take > 0 && j->cursor < j->n && n_entries < S->max_entries) {
-          const size_t i = j->cursor;
-          const uint64_t left = j->nchunk[i] - j->next_chunk[i];
-          if (left == 0) {  // resumed integrand with no samples left
-            ++j->cursor;
-            continue;
-          }
-          const uint64_t t = std::min(left, take);
-          Entry en;
-          en.item_begin = 0;  // filled when families are concatenated
-          en.fn = j->d_fns + i;
-          en.chunk_begin = j->next_chunk[i];
-          fam_ents[j->family[i]].push_back(en);
-          variant_of[en.fn] = j->fns[i].variant;
-          // remember the run length in item_begin for now
-          fam_ents[j->family[i]].back().item_begin = t;
-          ++n_entries;
-          j->next_chunk[i] += t;
-          j->chunks_issued += t;
-          take -= t;
-          budget -= t;
-          if (j->next_chunk[i] == j->nchunk[i]) ++j->cursor;
+    for (size_t q = 0; q < active.size(); ++q) {
+      if (take[q] == 0) continue;
+      auto &j = active[q];
+      ++jobs_in_iter;
+      uint64_t want = take[q];
+      while (want > 0 && j->cursor < j->n) {
+        const size_t i = j->cursor;
+        const uint64_t left_i = j->nchunk[i] - j->next_chunk[i];
+        if (left_i == 0) {  // resumed integrand with no samples left
+          ++j->cursor;
+          continue;
         }
-        j->last_seq = seq;
-        if (j->chunks_issued == j->chunks_total) {
-          S->to_merge.push_back(j);
-          if (cut_at_job_end) budget = 0;
-        } else {
-          still.push_back(j);
-        }
-        if (budget == 0) break;
+        const uint64_t t = std::min(left_i, want);
+        Entry en;
+        en.item_begin = t;  // the run length for now; item offsets come below
+        en.fn = j->d_fns + i;
+        en.chunk_begin = j->next_chunk[i];
+        fam_ents[j->family[i]].push_back(en);
+        variant_of[en.fn] = j->fns[i].variant;
+        ++n_entries;
+        j->next_chunk[i] += t;
+        j->chunks_issued += t;
+        want -= t;
+        if (j->next_chunk[i] == j->nchunk[i]) ++j->cursor;
       }
-      active.swap(still);
+      j->last_seq = seq;
+      if (j->chunks_issued == j->chunks_total) S->to_merge.push_back(j);
     }
     // concatenate by family, each family's runs ordered by variant (stable) so
     // co-resident warps mostly run the same code path, as in a plan;
@@ -895,6 +916,15 @@ zmc_status zmc_poll_any(zmc_ctx *ctx, uint64_t *job_ids, size_t cap, int32_t wai
   if (n) return ZMC_OK;
   if (S->stop) return set_error(ZMC_ECLOSED, "context is shutting down");
   return set_error(ZMC_EAGAIN, "no finished job");
+}
+
+zmc_status zmc_serving_fill(const uint64_t *chunks_left, size_t n_jobs, uint64_t budget,
+                            uint32_t share, uint64_t cut_backlog, uint64_t chunk_samples,
+                            uint64_t *take) {
+  if ((n_jobs > 0 && (!chunks_left || !take)) || chunk_samples == 0)
+    return set_error(ZMC_EINVAL, "zmc_serving_fill: null array or zero chunk_samples");
+  fill_launch(chunks_left, n_jobs, budget, share, cut_backlog, chunk_samples, take);
+  return ZMC_OK;
 }
 
 zmc_status zmc_serving_stats_get(zmc_ctx *ctx, zmc_serving_stats *out) {

@@ -120,6 +120,8 @@ _SIGS = {
     "zmc_eval_samples": ([_P, _P, ctypes.c_uint64, ctypes.c_uint32, _P], ctypes.c_int),
     "zmc_validate": ([_P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "zmc_variant_of": ([_P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "zmc_serving_fill": ([_P, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                          ctypes.c_uint64, _P], ctypes.c_int),
     "zmc_integrate_noalloc": ([_P, ctypes.c_size_t, _P, _P], ctypes.c_int),
     "zmc_udf_create": ([ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                         ctypes.POINTER(_P)], ctypes.c_int),
@@ -429,6 +431,17 @@ def zmc_variant_of(desc) -> np.ndarray:
     out["dim"] = codes & 0xF
     out["form"] = codes >> 8
     return out
+
+
+def zmc_serving_fill(chunks_left, budget: int, share: int = 0, cut_backlog: int = 0,
+                     chunk_samples: int = 4160) -> np.ndarray:
+    """Chunks each live job (oldest first) contributes to one serving launch
+    (zmc_serving_fill); host only."""
+    left = np.ascontiguousarray(chunks_left, dtype=np.uint64)
+    take = np.zeros(len(left), dtype=np.uint64)
+    _check(lib().zmc_serving_fill(left.ctypes.data, len(left), budget, share, cut_backlog,
+                                  chunk_samples, take.ctypes.data), "zmc_serving_fill")
+    return take
 
 
 # ------------------------------------------------------------------ convenience
