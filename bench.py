@@ -730,6 +730,70 @@ def fifo_bound(stream, capacity_gsps):
             "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
+def launch_model(jobs, capacity_gsps, chunk_samples=4160, budget_samples=2**31,
+                 cut_backlog=2**34, fixed_s=52e-6, build_s=30e-6, slots=2):
+    """p50 / p99 latency of a model of the serving loop on a job stream of
+    (arrival_s, samples, chunks): each launch holds at most budget_samples'
+    worth of chunks, filled oldest job first and ended at the first job it
+    completes while fewer than cut_backlog samples are left to issue (the
+    library's rule); a launch runs for fixed_s plus its samples at the kernels'
+    rate, which is set so that full launches deliver capacity_gsps; at most
+    `slots` launches are in flight, the next one built (build_s) as soon as a
+    slot is free and work is waiting; a job completes when the launch with its
+    last chunks ends.  It leaves out the merge, the copies and the host threads."""
+    budget = max(1, budget_samples // chunk_samples)
+    full_s = budget * chunk_samples / (capacity_gsps * 1e9)
+    if full_s <= fixed_s:
+        raise ValueError("a full launch must take longer than its fixed cost")
+    rate = budget * chunk_samples / (full_s - fixed_s)  # samples/s
+    n = len(jobs)
+    rem = [c for _, _, c in jobs]
+    per_chunk = [s / c if c else 0.0 for _, s, c in jobs]
+    lat = [0.0] * n
+    live, inflight = [], []  # inflight: (end_s, finished job indices), in order
+    arrived, t, gpu_free = 0, 0.0, 0.0
+    while True:
+        while inflight and inflight[0][0] <= t:
+            end, fin = inflight.pop(0)
+            for j in fin:
+                lat[j] = end - jobs[j][0]
+        while arrived < n and jobs[arrived][0] <= t:
+            if rem[arrived] == 0:
+                lat[arrived] = 0.0
+            else:
+                live.append(arrived)
+            arrived += 1
+        if live and len(inflight) < slots:
+            cut = sum(rem[j] * chunk_samples for j in live) < cut_backlog
+            left, samples, fin, keep = budget, 0.0, [], []
+            for j in live:
+                if left == 0:
+                    keep.append(j)
+                    continue
+                take = min(rem[j], left)
+                rem[j] -= take
+                left -= take
+                samples += take * per_chunk[j]
+                if rem[j] == 0:
+                    fin.append(j)
+                    if cut:
+                        left = 0
+                else:
+                    keep.append(j)
+            live = keep
+            gpu_free = max(t + build_s, gpu_free) + fixed_s + samples / rate
+            inflight.append((gpu_free, fin))
+            continue
+        nxt = [x for x in ((jobs[arrived][0] if arrived < n else None),
+                           (inflight[0][0] if inflight else None)) if x is not None]
+        if not nxt:
+            break
+        t = max(t, min(nxt))
+    lat.sort()
+    return {"capacity_gsps": capacity_gsps, "p50_ms": 1e3 * lat[len(lat) // 2],
+            "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]} if lat else None
+
+
 def run_functional(zmc, ctx):
     """Functional mode: one 4-D harmonic over a 1000-point lattice of its wave
     vector (k_1 = k_2 = k_3 = k_4 = kappa, kappa from 8.1 to 23.9, the Fig. 1
@@ -919,11 +983,20 @@ def run_serving_sweep(args):
     # the bound at the highest rate the sweep delivered (the capacity, when the
     # sweep holds a point above it)
     cap = max((r["samples_per_s"] for r in out if r), default=0.0)
-    for r in out:
+    chunk = 160 * (args.serving_quints or 26)
+    for rate, r in zip(args.serving_rates, out):
         if r:
             stream = r.pop("_stream")
             if cap > 0:
                 r["fifo_bound"] = fifo_bound(stream, cap)
+                # the same stream through a model of the launch loop (default
+                # launch rules only)
+                if not (args.serving_chunks or args.serving_share):
+                    jobs = [(at, W.total_samples(tab),
+                             int(np.sum((tab["n_samples"].astype(np.int64) + chunk - 1) // chunk)))
+                            for at, tab in W.serving_stream(rate, args.serving_seconds,
+                                                            max_fns=1000)]
+                    r["launch_model"] = launch_model(jobs, cap, chunk_samples=chunk)
     print(json.dumps({"serving_sweep": out, "seconds_per_rate": args.serving_seconds,
                       "job": "U{1..1000} mixed-style integrands, N ~ 10^U[4,7]"}), flush=True)
 
